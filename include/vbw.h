@@ -1,0 +1,165 @@
+/*
+ * vbw.h - C ABI of libvbw: overlap-save (OLS) fast-convolution filtering with a variable-bandwidth
+ * (VBW) filter whose DFT coefficients follow the hybrid frequency-sampling / optimization (HFSO)
+ * rule of Moryakova & Johansson, "Efficient Design and Implementation of Fast-Convolution-Based
+ * Variable-Bandwidth Filters". GB300 (sm_103a) only.
+ *
+ * The method (paper Sec. II and Sec. III-B):
+ *   - the input is cut into blocks of N samples that overlap by O = N - M samples (Sec. II);
+ *   - each block goes through an N-point DFT, a multiply by H(k,b), an N-point IDFT with +j and
+ *     1/N (eq. (OLS_dn)), and the first O outputs are discarded (Sec. II, steps 1-5);
+ *   - H(k,b) = H_R(k,b) exp(-j 2 pi k (L-1)/2 / N) with L - 1 = O (eq. (FS_Hk_exp)); H_R is 1 in
+ *     the passband, V(r) on the L_V transition bins at each band edge and 0 in the stopband
+ *     (eq. (FS_Hk_real)), so a bandwidth change moves the table V and computes nothing.
+ *
+ * Conventions used by every call:
+ *   - Samples are complex64: interleaved (re, im) float32 pairs, 8 bytes per sample.
+ *   - N is a power of two in [128, 2048]; overlap O is even with 0 < O < N; M = N - O.
+ *   - "band" is k1 of eq. (k_var): bins 0..k1-1 (and their mirrors) are passband, the transition
+ *     band is k1..k2 with k2 = k1 + L_V - 1, and 1 <= k1 <= N/2 - L_V - 1 (the paper's bounds
+ *     Delta_N/2 <= b_N <= N/2 - Delta_N/2 - 1 with b_N = k1 + Delta_N/2 - 1, L_V = Delta_N - 1).
+ *   - Stream alignment: O zero samples precede a stream's first sample, so output y(t) is the
+ *     filtered x(t) delayed by the filter's group delay O/2 and every input sample yields one
+ *     output sample. A final partial block is zero padded; only its valid outputs are written.
+ *   - Device pointers are caller-owned (e.g. PyTorch allocations); all filtering calls are
+ *     asynchronous on the CUDA stream given at stream or batch creation. Input and output
+ *     ranges must not overlap (an overlapping pair is VBW_ERR_INVALID_ARG).
+ *   - Errors are return codes; vbw_last_error() gives a thread-local message for the last
+ *     failing call on this thread.
+ */
+#ifndef VBW_H
+#define VBW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vbw_plan_s* vbw_plan_t;     /* library-owned: N, overlap, V and device tables */
+typedef struct vbw_stream_s* vbw_stream_t; /* library-owned: device tail, band, position    */
+typedef struct vbw_batch_s* vbw_batch_t;   /* library-owned: device work list of a batch     */
+
+typedef enum {
+    VBW_OK = 0,
+    VBW_ERR_INVALID_ARG = 1, /* a size, pointer or geometry outside the documented range   */
+    VBW_ERR_BAND_RANGE = 2,  /* band (k1) outside [1, N/2 - L_V - 1]                       */
+    VBW_ERR_NOMEM = 3,       /* a device or host allocation failed                          */
+    VBW_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error)     */
+    VBW_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                          */
+    VBW_ERR_BUSY = 6,        /* no free slot or memory for the request right now            */
+    VBW_ERR_STATE = 7,       /* call not allowed in the object's current state              */
+    VBW_ERR_UNSUPPORTED = 8  /* valid request that this build does not provide              */
+} vbw_status;
+
+enum { VBW_PREC_FP32 = 0 };
+
+/* Creates a plan for N-point OLS with the given overlap and the L_V transition samples
+ * V(0..L_V-1) of eq. (FS_Hk_real) (host array, read during the call; any finite values, the
+ * paper does not restrict them). The device keeps V rounded to float32 and the FFT twiddles,
+ * generated in FP64 on the GPU and rounded once. Needs a current CUDA device.
+ * Errors: VBW_ERR_INVALID_ARG (N not a power of two in [128, 2048], overlap odd or outside
+ * (0, N), L_V outside [1, N/2 - 2], non-finite V, precision unknown), VBW_ERR_NOMEM, VBW_ERR_CUDA. */
+vbw_status vbw_plan(int N, int overlap, const double* transition_samples, int L_V, int precision,
+                    vbw_plan_t* out);
+vbw_status vbw_plan_destroy(vbw_plan_t plan);
+
+/* Geometry of a plan: any output pointer may be NULL. */
+vbw_status vbw_plan_info(vbw_plan_t plan, int* N, int* overlap, int* L_V, int* M);
+
+/* Creates a filtering stream on the plan: device state holds the last O input samples (zeros at
+ * the start); the band (k1) is validated against the plan. cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream); every call on this stream object is ordered on it.
+ * Errors: VBW_ERR_BAND_RANGE, VBW_ERR_INVALID_ARG, VBW_ERR_NOMEM, VBW_ERR_CUDA. */
+vbw_status vbw_stream_create(vbw_plan_t plan, int band, void* cuda_stream, vbw_stream_t* out);
+vbw_status vbw_stream_destroy(vbw_stream_t s);
+
+/* Back to the stream's start: tail zeroed (stream-ordered), position 0, pending changes dropped,
+ * band set to `band`. */
+vbw_status vbw_stream_reset(vbw_stream_t s, int band);
+
+/* Bandwidth change (eq. (k_var) re-indexing, Sec. III-E: no coefficient is computed). Takes effect
+ * at the first block not yet submitted to vbw_filter, i.e. at a block boundary. */
+vbw_status vbw_set_bandwidth(vbw_stream_t s, int band);
+
+/* Bandwidth change at an absolute block index of the stream (block >= blocks submitted so far).
+ * A later call for the same block replaces the earlier one. Errors: VBW_ERR_BAND_RANGE,
+ * VBW_ERR_INVALID_ARG (block in the past). */
+vbw_status vbw_set_bandwidth_at(vbw_stream_t s, int64_t block, int band);
+
+/* Filters the next nblocks * M samples of the stream: `in` and `out` are device complex64 arrays
+ * of nblocks * M samples (Sec. II: block m reads the O previous samples and these M). nblocks = 0
+ * is a no-op. Asynchronous; `in` must stay valid until the stream's work completes.
+ * Errors: VBW_ERR_INVALID_ARG (NULL or overlapping pointers, nblocks < 0), VBW_ERR_STATE (after
+ * vbw_flush), VBW_ERR_CUDA. */
+vbw_status vbw_filter(vbw_stream_t s, const void* in, void* out, int64_t nblocks);
+
+/* Ends the stream with a partial block of nvalid samples (0 <= nvalid < M): the block is zero
+ * padded after them and only nvalid outputs are written to `out`. After it only vbw_stream_reset
+ * is allowed. nvalid = 0 only ends the stream. */
+vbw_status vbw_flush(vbw_stream_t s, const void* in, void* out, int nvalid);
+
+/* Same as vbw_filter but `in` and `out` are HOST arrays (pageable or pinned): the call copies the
+ * input to the device, filters and copies the result back, pipelined in chunks on the stream's
+ * CUDA stream with library-owned device staging, and returns when `out` holds the result. */
+vbw_status vbw_filter_host(vbw_stream_t s, const void* in, void* out, int64_t nblocks);
+
+/* Blocks submitted so far (the absolute index of the next block). */
+vbw_status vbw_stream_position(vbw_stream_t s, int64_t* blocks);
+
+/* Checkpoint / resume of a stream: the serialized state is (N, overlap, band, position, pending
+ * changes, flushed flag, the O-sample tail). vbw_stream_save synchronizes the stream's CUDA
+ * stream. With host_buf == NULL it only reports the size in *bytes. vbw_stream_restore needs a
+ * stream created on a plan with the same N, overlap and L_V. */
+vbw_status vbw_stream_save(vbw_stream_t s, void* host_buf, size_t* bytes);
+vbw_status vbw_stream_restore(vbw_stream_t s, const void* host_buf, size_t bytes);
+
+/* One signal of a batch: a whole stream filtered from a zero history (the paper's stream start).
+ * band_per_block (host, ceil(nsamples / M) entries) gives k1 for every block; when it is NULL
+ * every block uses `band`. */
+typedef struct {
+    vbw_plan_t plan;               /* geometry and transition table of this signal          */
+    const void* in;                /* device complex64 [nsamples]                           */
+    void* out;                     /* device complex64 [nsamples]                           */
+    int64_t nsamples;              /* >= 0; the final partial block is zero padded          */
+    int32_t band;                  /* k1 for every block when band_per_block is NULL        */
+    const int32_t* band_per_block; /* host, optional                                       */
+} vbw_signal;
+
+/* Prepares a batch of signals, which may use different plans (mixed N): validates every band,
+ * builds and uploads the device work list (synchronous, allocates). The batch records the
+ * signal pointers; the caller keeps those arrays allocated while the batch is used. */
+vbw_status vbw_batch_create(const vbw_signal* signals, int nsignals, vbw_batch_t* out);
+
+/* Runs a prepared batch on cuda_stream: asynchronous, no allocation, no host-device copy, so it
+ * can be captured in a CUDA graph. */
+vbw_status vbw_batch_run(vbw_batch_t batch, void* cuda_stream);
+
+/* Runs a prepared batch from HOST buffers: host_in[i] and host_out[i] hold signal i's nsamples
+ * samples (pinned memory gives overlapped copies; pageable memory works but serializes them).
+ * The batch's device in/out arrays serve as staging. Copies in, kernels and copies out are
+ * pipelined over groups of signals on library-owned streams that start after the work already
+ * queued on cuda_stream; the call returns when every host_out is written. */
+vbw_status vbw_batch_run_host(vbw_batch_t batch, const void* const* host_in, void* const* host_out,
+                              void* cuda_stream);
+vbw_status vbw_batch_destroy(vbw_batch_t batch);
+
+/* Number of kernel launches the last vbw_batch_run of this batch issued (for accounting). */
+vbw_status vbw_batch_launches(vbw_batch_t batch, int* launches);
+
+/* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
+ * produced by the same device code and register layout, to host_out (N floats). Synchronous. */
+vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* vbw_last_error(void);
+
+/* Library version string. */
+const char* vbw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBW_H */

@@ -1,0 +1,129 @@
+// Shared device-side definitions of libvbw: work descriptors, compile-time trigonometry and the
+// per-N thread layout of the fused OLS kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace vbw {
+
+// ---------------------------------------------------------------------------------------------
+// Compile-time unrolling helper: calls f(std::integral_constant<int, i>) for i = B, B+S, ... < E.
+template <int B, int E, int S = 1, class F>
+__host__ __device__ __forceinline__ constexpr void static_for(F&& f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + S, E, S>(f);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Compile-time cos/sin of 2*pi*p/q for the constant twiddles inside the register DFT codelets.
+// The angle is folded into [0, pi/4] with exact integer symmetries (f -> 1-f, 1/2-f, 1/4-f),
+// then evaluated with the Maclaurin series in double precision and rounded to float once at the
+// point of use. (The run-time twiddle tables are generated on the GPU in FP64 instead.)
+struct CosSin {
+    double c, s;
+};
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+constexpr double maclaurin_cos(double x)
+{
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < 24; ++i) {
+        term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double maclaurin_sin(double x)
+{
+    double term = x, sum = x;
+    for (int i = 1; i < 24; ++i) {
+        term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr CosSin cos_sin_2pi(long p, long q)
+{
+    p %= q;
+    if (p < 0) p += q;
+    bool neg_s = false, neg_c = false, swap = false;
+    if (2 * p > q) { p = q - p; neg_s = true; }             // 1 - f: sin changes sign
+    if (4 * p > q) { p = q - 2 * p; q = 2 * q; neg_c = true; }  // 1/2 - f: cos changes sign
+    if (8 * p > q) { p = q - 4 * p; q = 4 * q; swap = true; }   // 1/4 - f: sin <-> cos
+    const double x = 2.0 * kPi * static_cast<double>(p) / static_cast<double>(q);
+    double c = maclaurin_cos(x), s = maclaurin_sin(x);
+    if (swap) { const double t = c; c = s; s = t; }
+    if (neg_c) c = -c;
+    if (neg_s) s = -s;
+    return CosSin{c, s};
+}
+
+// ---------------------------------------------------------------------------------------------
+// Thread layout of the fused FP32 OLS kernel for each N (see ols_fp32.cuh):
+//   T threads cooperate on one block, each holding E = N/T samples; N = E * T with T | E.
+//   Pass 1 is an E-point register DFT per thread, pass 2 does E/T T-point register DFTs per
+//   thread after a shared-memory transpose. 32/T blocks share one warp.
+template <int N>
+struct Layout;
+template <> struct Layout<128>  { static constexpr int E = 16, T = 8;  };
+template <> struct Layout<256>  { static constexpr int E = 16, T = 16; };
+template <> struct Layout<512>  { static constexpr int E = 32, T = 16; };
+template <> struct Layout<1024> { static constexpr int E = 32, T = 32; };
+template <> struct Layout<2048> { static constexpr int E = 64, T = 32; };
+
+// Host mirror of Layout<N>::T (the twiddle table layout depends on it).
+inline int layout_T(int N)
+{
+    switch (N) {
+    case 128: return 8;
+    case 256: return 16;
+    case 512: return 16;
+    case 1024: return 32;
+    case 2048: return 32;
+    default: return 0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Work descriptors.
+
+// One stream segment filtered by a launch. Block m of the job reads x(mM - O .. mM + M - 1) of
+// the segment (negative indices come from tail_in, or zeros) and writes y(mM .. mM + M - 1).
+struct OlsJob {
+    const float2* in;      // device, nsamp samples
+    float2* out;           // device, nsamp samples
+    const float2* tail_in; // device, O samples preceding in[0]; nullptr = zeros
+    float2* tail_out;      // device, receives the last O samples of tail_in ++ in; nullptr = none
+    const int32_t* band;   // device, k1 per block; nullptr = band0 (plus inline changes)
+    int64_t nsamp;
+    int32_t band0;
+    int32_t pad_;
+};
+
+constexpr int kInlineChanges = 16;
+
+struct OlsArgs {
+    const OlsJob* jobs;   // device job array (batch mode); nullptr = single job `job`
+    const int2* tiles;    // device: per warp-tile (job index, first block); batch mode only
+    int64_t ntiles;       // warp-tiles in this launch
+    OlsJob job;           // single-job mode
+    int32_t nchg;         // single-job mode: inline band changes (block, band), sorted by block
+    int32_t chg_band[kInlineChanges];
+    int64_t chg_block[kInlineChanges];
+    const float2* tw;     // device twiddle table [ka][n2] = W_N^{n2 ka} / sqrt(N), N entries
+    const float* V;       // device transition samples, L_V floats
+    int32_t overlap;
+    int32_t LV;
+};
+
+}  // namespace vbw

@@ -1,0 +1,359 @@
+"""Thin Python binding of libvbw (include/vbw.h), argument marshalling only.
+
+Functions named ``vbw_*`` mirror the C entry points one to one; the classes ``Plan``, ``Stream``
+and ``Batch`` only hold handles and turn tensors into pointers. Every filtering step runs in the
+CUDA kernels of the library; there is no fallback: if ``libvbw.so`` is missing or fails to load,
+every call raises ``VbwError``.
+
+Device arrays are passed as ``torch.Tensor`` (complex64, CUDA, contiguous) or as raw integer
+device pointers; host arrays as ``numpy.ndarray``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvbw.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "vbw.h")
+
+VBW_OK = 0
+STATUS_NAMES = {0: "VBW_OK", 1: "VBW_ERR_INVALID_ARG", 2: "VBW_ERR_BAND_RANGE", 3: "VBW_ERR_NOMEM",
+                4: "VBW_ERR_CUDA", 5: "VBW_ERR_TIMEOUT", 6: "VBW_ERR_BUSY", 7: "VBW_ERR_STATE",
+                8: "VBW_ERR_UNSUPPORTED"}
+VBW_PREC_FP32 = 0
+
+
+class VbwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class vbw_signal(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("nsamples", ctypes.c_int64), ("band", ctypes.c_int32),
+                ("band_per_block", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/vbw.h declares."""
+    text = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"\b(vbw_[a-z_A-Z0-9]+)\s*\(", text)))
+
+
+def lib():
+    """Loads libvbw.so (built by paper_2406_14116_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise VbwError(-1, f"{LIB_PATH} is missing: run paper_2406_14116_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, p, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "vbw_plan": [i32, i32, p, i32, i32, pp],
+        "vbw_plan_destroy": [p],
+        "vbw_plan_info": [p, p, p, p, p],
+        "vbw_stream_create": [p, i32, p, pp],
+        "vbw_stream_destroy": [p],
+        "vbw_stream_reset": [p, i32],
+        "vbw_set_bandwidth": [p, i32],
+        "vbw_set_bandwidth_at": [p, i64, i32],
+        "vbw_filter": [p, p, p, i64],
+        "vbw_flush": [p, p, p, i32],
+        "vbw_filter_host": [p, p, p, i64],
+        "vbw_stream_position": [p, p],
+        "vbw_stream_save": [p, p, ctypes.POINTER(sz)],
+        "vbw_stream_restore": [p, p, sz],
+        "vbw_batch_create": [p, i32, pp],
+        "vbw_batch_run": [p, p],
+        "vbw_batch_run_host": [p, p, p, p],
+        "vbw_batch_destroy": [p],
+        "vbw_batch_launches": [p, p],
+        "vbw_debug_export_HR": [p, i32, p],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.vbw_last_error.argtypes = []
+    L.vbw_last_error.restype = ctypes.c_char_p
+    L.vbw_version.argtypes = []
+    L.vbw_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def vbw_last_error() -> str:
+    return lib().vbw_last_error().decode()
+
+
+def vbw_version() -> str:
+    return lib().vbw_version().decode()
+
+
+def _check(code: int):
+    if code != VBW_OK:
+        raise VbwError(code, vbw_last_error())
+
+
+def _dev_ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        import torch
+        if x.dtype != torch.complex64:
+            raise ValueError("expected complex64 samples")
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _host_ptr(a: np.ndarray):
+    if not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous host array")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(cuda_stream) -> int:
+    if cuda_stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(cuda_stream, int):
+        return cuda_stream
+    return int(cuda_stream.cuda_stream)
+
+
+# ---- C entry points ---------------------------------------------------------------------------
+
+def vbw_plan(N: int, overlap: int, transition_samples, precision: int = VBW_PREC_FP32) -> int:
+    V = np.ascontiguousarray(np.asarray(transition_samples, dtype=np.float64))
+    h = ctypes.c_void_p()
+    _check(lib().vbw_plan(N, overlap, _host_ptr(V), len(V), precision, ctypes.byref(h)))
+    return h.value
+
+
+def vbw_plan_destroy(plan: int):
+    _check(lib().vbw_plan_destroy(plan))
+
+
+def vbw_plan_info(plan: int):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().vbw_plan_info(plan, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)   # N, overlap, L_V, M
+
+
+def vbw_stream_create(plan: int, band: int, cuda_stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().vbw_stream_create(plan, band, _stream_handle(cuda_stream), ctypes.byref(h)))
+    return h.value
+
+
+def vbw_stream_destroy(s: int):
+    _check(lib().vbw_stream_destroy(s))
+
+
+def vbw_stream_reset(s: int, band: int):
+    _check(lib().vbw_stream_reset(s, band))
+
+
+def vbw_set_bandwidth(s: int, band: int):
+    _check(lib().vbw_set_bandwidth(s, band))
+
+
+def vbw_set_bandwidth_at(s: int, block: int, band: int):
+    _check(lib().vbw_set_bandwidth_at(s, block, band))
+
+
+def vbw_filter(s: int, inp, out, nblocks: int):
+    _check(lib().vbw_filter(s, _dev_ptr(inp), _dev_ptr(out), nblocks))
+
+
+def vbw_flush(s: int, inp, out, nvalid: int):
+    _check(lib().vbw_flush(s, _dev_ptr(inp), _dev_ptr(out), nvalid))
+
+
+def vbw_filter_host(s: int, inp: np.ndarray, out: np.ndarray, nblocks: int):
+    _check(lib().vbw_filter_host(s, _host_ptr(inp), _host_ptr(out), nblocks))
+
+
+def vbw_stream_position(s: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().vbw_stream_position(s, ctypes.byref(v)))
+    return v.value
+
+
+def vbw_stream_save(s: int) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().vbw_stream_save(s, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().vbw_stream_save(s, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def vbw_stream_restore(s: int, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib().vbw_stream_restore(s, buf, len(state)))
+
+
+def vbw_batch_create(signals) -> int:
+    """signals: sequence of (plan, in, out, nsamples, band, band_per_block or None)."""
+    arr = (vbw_signal * max(1, len(signals)))()
+    keep = []
+    for i, (plan, inp, out, nsamp, band, bpb) in enumerate(signals):
+        ptr = None
+        if bpb is not None:
+            bpb = np.ascontiguousarray(np.asarray(bpb, dtype=np.int32))
+            keep.append(bpb)
+            ptr = bpb.ctypes.data
+        arr[i] = vbw_signal(plan, _dev_ptr(inp), _dev_ptr(out), int(nsamp), int(band), ptr)
+    h = ctypes.c_void_p()
+    _check(lib().vbw_batch_create(arr, len(signals), ctypes.byref(h)))
+    return h.value
+
+
+def vbw_batch_run(b: int, cuda_stream=None):
+    _check(lib().vbw_batch_run(b, _stream_handle(cuda_stream)))
+
+
+def vbw_batch_run_host(b: int, host_in, host_out, cuda_stream=None):
+    """host_in / host_out: sequences of C-contiguous numpy arrays (one per signal)."""
+    n = len(host_in)
+    ins = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in host_in])
+    outs = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in host_out])
+    _check(lib().vbw_batch_run_host(b, ins, outs, _stream_handle(cuda_stream)))
+
+
+def vbw_batch_destroy(b: int):
+    _check(lib().vbw_batch_destroy(b))
+
+
+def vbw_batch_launches(b: int) -> int:
+    v = ctypes.c_int()
+    _check(lib().vbw_batch_launches(b, ctypes.byref(v)))
+    return v.value
+
+
+def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
+    N = vbw_plan_info(plan)[0]
+    out = np.empty(N, dtype=np.float32)
+    _check(lib().vbw_debug_export_HR(plan, band, _host_ptr(out)))
+    return out
+
+
+# ---- handle holders ---------------------------------------------------------------------------
+
+class Plan:
+    def __init__(self, N: int, overlap: int, V, precision: int = VBW_PREC_FP32):
+        self.handle = vbw_plan(N, overlap, V, precision)
+        self.N, self.overlap, self.LV, self.M = vbw_plan_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            vbw_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    def __init__(self, plan: Plan, band: int, cuda_stream=None):
+        self.plan = plan
+        self.handle = vbw_stream_create(plan.handle, band, cuda_stream)
+
+    def filter(self, inp, out, nblocks: int | None = None):
+        if nblocks is None:
+            nblocks = inp.numel() // self.plan.M
+        vbw_filter(self.handle, inp, out, nblocks)
+
+    def flush(self, inp, out, nvalid: int):
+        vbw_flush(self.handle, inp, out, nvalid)
+
+    def filter_host(self, inp: np.ndarray, out: np.ndarray, nblocks: int | None = None):
+        if nblocks is None:
+            nblocks = len(inp) // self.plan.M
+        vbw_filter_host(self.handle, inp, out, nblocks)
+
+    def set_bandwidth(self, band: int):
+        vbw_set_bandwidth(self.handle, band)
+
+    def set_bandwidth_at(self, block: int, band: int):
+        vbw_set_bandwidth_at(self.handle, block, band)
+
+    def reset(self, band: int):
+        vbw_stream_reset(self.handle, band)
+
+    @property
+    def position(self) -> int:
+        return vbw_stream_position(self.handle)
+
+    def save(self) -> bytes:
+        return vbw_stream_save(self.handle)
+
+    def restore(self, state: bytes):
+        vbw_stream_restore(self.handle, state)
+
+    def close(self):
+        if self.handle:
+            vbw_stream_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A prepared batch: signals = [(Plan, in_tensor, out_tensor, band or per-block array)]."""
+
+    def __init__(self, signals):
+        rows = []
+        for plan, inp, out, band in signals:
+            n = int(inp.numel())
+            if np.ndim(band) == 0:
+                rows.append((plan.handle, inp, out, n, int(band), None))
+            else:
+                b = np.asarray(band, dtype=np.int32)
+                rows.append((plan.handle, inp, out, n, int(b[0]) if len(b) else 1, b))
+        self.handle = vbw_batch_create(rows)
+        self.signals = signals
+
+    def run(self, cuda_stream=None):
+        vbw_batch_run(self.handle, cuda_stream)
+
+    def run_host(self, host_in, host_out, cuda_stream=None):
+        vbw_batch_run_host(self.handle, host_in, host_out, cuda_stream)
+
+    @property
+    def launches(self) -> int:
+        return vbw_batch_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            vbw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
