@@ -4,8 +4,16 @@
 //   forward (INV = false): A(k) = sum_n a(n) exp(-j 2 pi n k / R)
 //   inverse (INV = true):  A(k) = sum_n a(n) exp(+j 2 pi n k / R)      (no 1/R)
 // as radix-2 decimation-in-time stages over a bit-reversed copy. All indices are compile-time
-// constants, so the bit reversal is register renaming and the twiddles are FFMA immediates;
-// multiplications by +-1 and +-j are turned into sign flips and swaps.
+// constants, so the bit reversal is register renaming and the twiddles are FFMA immediates.
+//
+// Butterfly cost (FP32 instructions per (u, v) pair):
+//   w = 1, -1, +-j                  4 adds (signs folded)
+//   w = (+-1 +-j)/sqrt(2)           2 adds + 4 FFMA
+//   any other w = c + j s           "tangent" form w v = c ((v.x - t v.y) + j (v.y + t v.x)) with
+//                                   t = s/c (or the cotangent form when |s| > |c|, so |t| <= 1):
+//                                   2 FFMA for the rotation + 4 FFMA for u +- c(.)  = 6
+// fft_reg_gain<R, INV>(a, g) is fft_reg on the input g(n) a(n) (real gains), with the gains
+// folded into the first stage: g_lo a_lo +- g_hi a_hi = 2 FMUL + 4 FFMA per pair.
 #pragma once
 
 #include "vbw_common.cuh"
@@ -40,53 +48,110 @@ constexpr int bit_reverse(int i)
     return r;
 }
 
-// v * exp(-+ j 2 pi J / LEN): '-' for the forward transform, '+' for the inverse.
+constexpr double cabs_d(double x) { return x < 0 ? -x : x; }
+
+// (u, v) <- (u + w v, u - w v) with w = exp(-+ j 2 pi J / LEN) ('-' forward, '+' inverse).
 template <int LEN, int J, bool INV>
-__device__ __forceinline__ float2 twiddle_const(float2 v)
+__device__ __forceinline__ void bfly(float2& u, float2& v)
 {
     constexpr int j = ((J % LEN) + LEN) % LEN;
     if constexpr (j == 0) {
-        return v;
+        const float2 a = u, b = v;
+        u = make_float2(a.x + b.x, a.y + b.y);
+        v = make_float2(a.x - b.x, a.y - b.y);
     } else if constexpr (2 * j == LEN) {
-        return make_float2(-v.x, -v.y);
-    } else if constexpr (4 * j == LEN) {          // fwd: -j, inv: +j
-        if constexpr (INV) return make_float2(-v.y, v.x);
-        else return make_float2(v.y, -v.x);
-    } else if constexpr (4 * j == 3 * LEN) {      // fwd: +j, inv: -j
-        if constexpr (INV) return make_float2(v.y, -v.x);
-        else return make_float2(-v.y, v.x);
+        const float2 a = u, b = v;
+        u = make_float2(a.x - b.x, a.y - b.y);
+        v = make_float2(a.x + b.x, a.y + b.y);
+    } else if constexpr (4 * j == LEN || 4 * j == 3 * LEN) {
+        // w = -j (forward, j = LEN/4) or +j; the inverse flips the sign.
+        constexpr bool minus_j = (4 * j == LEN) != INV;
+        const float2 a = u, b = v;
+        if constexpr (minus_j) {   // w v = (v.y, -v.x)
+            u = make_float2(a.x + b.y, a.y - b.x);
+            v = make_float2(a.x - b.y, a.y + b.x);
+        } else {                   // w v = (-v.y, v.x)
+            u = make_float2(a.x - b.y, a.y + b.x);
+            v = make_float2(a.x + b.y, a.y - b.x);
+        }
     } else {
         constexpr CosSin cs = cos_sin_2pi(j, LEN);
-        constexpr float wr = static_cast<float>(cs.c);
-        constexpr float wi = INV ? static_cast<float>(cs.s) : -static_cast<float>(cs.s);
-        return make_float2(fmaf(v.x, wr, -v.y * wi), fmaf(v.x, wi, v.y * wr));
+        constexpr double c = cs.c;
+        constexpr double s = INV ? cs.s : -cs.s;
+        const float2 a = u, b = v;
+        if constexpr (8 * j == LEN || 8 * j == 3 * LEN || 8 * j == 5 * LEN || 8 * j == 7 * LEN) {
+            // w = h (sc + j ss), sc, ss in {+1, -1}, h = sqrt(1/2)
+            constexpr float h = static_cast<float>(cabs_d(c));
+            constexpr float sc = c > 0 ? 1.f : -1.f;
+            constexpr float ss = s > 0 ? 1.f : -1.f;
+            const float p = sc * b.x - ss * b.y;      // sign products fold into FADD
+            const float q = sc * b.y + ss * b.x;
+            u = make_float2(fmaf(h, p, a.x), fmaf(h, q, a.y));
+            v = make_float2(fmaf(-h, p, a.x), fmaf(-h, q, a.y));
+        } else if constexpr (cabs_d(c) >= cabs_d(s)) {
+            constexpr float cf = static_cast<float>(c);
+            constexpr float t = static_cast<float>(s / c);
+            const float p = fmaf(-t, b.y, b.x);
+            const float q = fmaf(t, b.x, b.y);
+            u = make_float2(fmaf(cf, p, a.x), fmaf(cf, q, a.y));
+            v = make_float2(fmaf(-cf, p, a.x), fmaf(-cf, q, a.y));
+        } else {
+            constexpr float sf = static_cast<float>(s);
+            constexpr float t = static_cast<float>(c / s);
+            const float p = fmaf(t, b.x, -b.y);
+            const float q = fmaf(t, b.y, b.x);
+            u = make_float2(fmaf(sf, p, a.x), fmaf(sf, q, a.y));
+            v = make_float2(fmaf(-sf, p, a.x), fmaf(-sf, q, a.y));
+        }
     }
+}
+
+// Radix-2 DIT stages of length FIRST_LEN..R over the bit-reversed array b.
+template <int R, int FIRST_LOG, bool INV>
+__device__ __forceinline__ void dit_stages(float2 (&b)[R])
+{
+    static_for<FIRST_LOG, ilog2(R) + 1>([&](auto sl) {
+        constexpr int len = 1 << decltype(sl)::value;
+        constexpr int half = len / 2;
+        static_for<0, R, len>([&](auto g) {
+            static_for<0, half>([&](auto jj) {
+                constexpr int lo = decltype(g)::value + decltype(jj)::value;
+                bfly<len, decltype(jj)::value, INV>(b[lo], b[lo + half]);
+            });
+        });
+    });
 }
 
 template <int R, bool INV>
 __device__ __forceinline__ void fft_reg(float2 (&a)[R])
 {
     static_assert((R & (R - 1)) == 0 && R >= 1, "radix-2 codelet needs a power of two");
-    if constexpr (R == 1) {
-        return;
-    } else {
+    if constexpr (R > 1) {
         float2 b[R];
         static_for<0, R>([&](auto i) { b[bit_reverse<R>(decltype(i)::value)] = a[i]; });
-        static_for<1, ilog2(R) + 1>([&](auto s) {
-            constexpr int len = 1 << decltype(s)::value;
-            constexpr int half = len / 2;
-            static_for<0, R, len>([&](auto g) {
-                static_for<0, half>([&](auto jj) {
-                    constexpr int lo = decltype(g)::value + decltype(jj)::value;
-                    const float2 u = b[lo];
-                    const float2 w = twiddle_const<len, decltype(jj)::value, INV>(b[lo + half]);
-                    b[lo] = cadd(u, w);
-                    b[lo + half] = csub(u, w);
-                });
-            });
-        });
+        dit_stages<R, 1, INV>(b);
         static_for<0, R>([&](auto i) { a[i] = b[i]; });
     }
+}
+
+// fft_reg of (g(n) a(n)): the first DIT stage pairs natural indices (i, i + R/2), which sit at
+// bit-reversed positions (2m, 2m + 1); the gains enter there as FMUL/FFMA factors.
+template <int R, bool INV>
+__device__ __forceinline__ void fft_reg_gain(float2 (&a)[R], const float (&g)[R])
+{
+    static_assert(R >= 2 && (R & (R - 1)) == 0, "radix-2 codelet needs a power of two >= 2");
+    float2 b[R];
+    static_for<0, R / 2>([&](auto m) {
+        constexpr int lo = 2 * decltype(m)::value, hi = lo + 1;
+        constexpr int nlo = bit_reverse<R>(lo), nhi = bit_reverse<R>(hi);
+        const float2 x = a[nlo], y = a[nhi];
+        const float gl = g[nlo], gh = g[nhi];
+        const float px = gl * x.x, py = gl * x.y;
+        b[lo] = make_float2(fmaf(gh, y.x, px), fmaf(gh, y.y, py));
+        b[hi] = make_float2(fmaf(-gh, y.x, px), fmaf(-gh, y.y, py));
+    });
+    if constexpr (R > 2) dit_stages<R, 2, INV>(b);
+    static_for<0, R>([&](auto i) { a[i] = b[i]; });
 }
 
 }  // namespace vbw

@@ -4,13 +4,16 @@
 // Decomposition (four-step FFT, N = E * T):
 //   thread t of a block holds x(T n1 + t), n1 = 0..E-1 (coalesced loads),
 //   F1  E-point register DFT over n1                      -> A(ka, t)
-//   F2  A(ka, t) *= W_N^{t ka} / sqrt(N)                  (shared-memory table)
+//   F2  A(ka, t) *= W_N^{t ka}                            (shared-memory table; ka = 0 is 1)
 //   F3  shared-memory transpose: thread t now owns ka = s T + t (s < E/T), every n2
 //   F4  T-point register DFTs over n2                     -> X(ka + E k'), k' = 0..T-1
-//   H   X(k) *= H_R(k) from (k1, L_V, V): passband untouched, transition scaled, stopband zeroed
+//   H   X(k) *= H_R(k) / N: the real gains come from a per-warp table g(kk), kk = min(k, N-k),
+//       rebuilt from (k1, L_V, V) only when the block's band differs from the table's; they are
+//       folded into the first stage of I1, so passband and stopband bins cost no extra work, and
+//       they carry the 1/N of eq. (OLS_dn) (a power of two, so the scaling is exact)
 //   I1  T-point inverse register DFTs over k'             -> B(ka, n2)
 //   I3  transpose back: thread t owns n2 = t, every ka
-//   I2  B(ka, t) *= conj(W_N^{t ka}) / sqrt(N)            (the two 1/sqrt(N) give eq. (OLS_dn)'s 1/N)
+//   I2  B(ka, t) *= conj(W_N^{t ka})
 //   I4  E-point inverse register DFT over ka              -> z(T n1 + t)
 // The linear phase exp(-j 2 pi k D / N), D = O/2, of eq. (FS_Hk_exp) is an exact circular shift of
 // the IDFT output by D samples, so nothing multiplies it: the kept outputs w(O..N-1) of Sec. II
@@ -27,49 +30,71 @@ struct OlsGeom {
     static constexpr int T = Layout<N>::T;
     static constexpr int B = 32 / T;    // blocks per warp
     static constexpr int S = E / T;     // pass-2 DFTs per thread
-    static constexpr int ROW = T + 1;   // padded transpose row (float2 elements)
-    // per-block transpose buffer; for T = 8 two blocks share a half-warp, so their buffers are
-    // offset by 8 elements mod 16 to keep 64-bit accesses conflict-free
+    // padded transpose row (float2 elements): T + 2 keeps every row 16-byte aligned, so the
+    // row side of each transpose moves two samples per 128-bit access, and offsets consecutive
+    // rows by 16 bytes mod 128, so those accesses are conflict-free
+    static constexpr int ROW = T + 2;
+    // per-block transpose buffer; for T = 8 two blocks share a half-warp on the column side, so
+    // their buffers are offset by 64 bytes mod 128
     static constexpr int BLK = E * ROW + ((T == 8) ? 8 : 0);
-    static constexpr int WARP_BUF = B * BLK;
+    // twiddle table row of thread t: W_N^{t ka}, ka = 0..E-1, padded to E + 2
+    static constexpr int TWROW = E + 2;
+    static constexpr int TW = T * TWROW;
+    // per-block gain table g(kk), kk = 0..N/2; when several blocks share a warp their tables are
+    // offset by T banks so the lane groups never collide
+    static constexpr int GT_MIN = N / 2 + 1;
+    static constexpr int GT = (B == 1) ? ((GT_MIN + 3) & ~3)
+                                       : GT_MIN + ((T - GT_MIN % 32) % 32 + 32) % 32;
+    static constexpr size_t WARP_BYTES =
+        (sizeof(float2) * B * BLK + sizeof(float) * B * GT + 15) / 16 * 16;
     static_assert(E * T == N && E % T == 0, "layout must satisfy N = E*T with T | E");
+    static_assert(BLK % 2 == 0 && T % 2 == 0, "transpose rows must stay 16-byte aligned");
 };
 
-// Shared memory of one CTA: twiddles (N float2), V (L_V floats, padded to 4), transpose buffers.
+// Shared memory of one CTA: twiddles (T rows of E + 2 float2), then per warp the transpose
+// buffers and gains.
 template <int N>
-__host__ __device__ inline size_t ols_smem_bytes(int warps, int LV)
+__host__ __device__ inline size_t ols_smem_bytes(int warps)
 {
-    const int lvpad = (LV + 3) & ~3;
-    return sizeof(float2) * (size_t)N + sizeof(float) * (size_t)lvpad +
-           sizeof(float2) * (size_t)warps * OlsGeom<N>::WARP_BUF;
+    return sizeof(float2) * (size_t)OlsGeom<N>::TW + (size_t)warps * OlsGeom<N>::WARP_BYTES;
 }
 
-// H_R(k) of eq. (FS_Hk_real) applied to the spectrum held in the pass-2 layout:
-// c[s][k'] = X(k) with k = s T + t + E k'. For k' < T/2, k < N/2; otherwise the mirror
-// index N - k is used, so H_R(N - k) = H_R(k). With r = min(k, N-k) - k1: r < 0 passband (x1),
-// 0 <= r < L_V transition (x V(r)), r >= L_V stopband (x0; k = N/2 is always stopband).
+// g(kk) = H_R / N with H_R of eq. (FS_Hk_real) on the non-negative half, kk = 0..N/2:
+// kk <= k1 - 1 passband (1), k1 <= kk <= k1 + L_V - 1 transition (V(kk - k1)), else stopband (0).
+// 1/N is a power of two, so g * N recovers H_R exactly. Written by the T lanes of one lane group.
 template <int N>
-__device__ __forceinline__ void apply_band(float2 (&c)[OlsGeom<N>::S][OlsGeom<N>::T], int t, int k1,
-                                           int LV, const float* V)
+__device__ __forceinline__ void build_gains(float* gtab, int t, int k1, int LV, const float* V)
+{
+    constexpr int T = OlsGeom<N>::T;
+    constexpr float inv_n = 1.0f / N;
+    for (int kk = t; kk <= N / 2; kk += T) {
+        const int r = kk - k1;
+        gtab[kk] = (r < 0 ? 1.f : (r < LV ? V[r] : 0.f)) * inv_n;
+    }
+}
+
+// L2 prefetch of a contiguous byte range with one bulk-copy instruction (16-byte aligned start,
+// size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Gains for the pass-2 layout: g[s][k'] = H_R(k), k = s T + t + E k'. For k' < T/2, k < N/2;
+// otherwise the mirror N - k is used, which makes H_R(N - k) = H_R(k).
+template <int N>
+__device__ __forceinline__ void load_gains(float (&g)[OlsGeom<N>::S][OlsGeom<N>::T], const float* gtab,
+                                           int t)
 {
     constexpr int E = OlsGeom<N>::E, T = OlsGeom<N>::T, S = OlsGeom<N>::S;
+    const float* lo = gtab + t;
+    const float* hi = gtab + (N - t);
     static_for<0, S>([&](auto s) {
         static_for<0, T>([&](auto kp) {
             constexpr int KP = decltype(kp)::value;
             constexpr int base = decltype(s)::value * T + E * KP;
-            int kk;
-            if constexpr (KP < T / 2) kk = base + t;
-            else kk = N - base - t;
-            const int r = kk - k1;
-            float2 v = c[s][kp];
-            if (r >= LV) {
-                v = make_float2(0.f, 0.f);
-            } else if (r >= 0) {
-                const float g = V[r];
-                v.x *= g;
-                v.y *= g;
-            }
-            c[s][kp] = v;
+            if constexpr (KP < T / 2) g[s][kp] = lo[base];
+            else g[s][kp] = hi[-base];
         });
     });
 }
@@ -77,29 +102,89 @@ __device__ __forceinline__ void apply_band(float2 (&c)[OlsGeom<N>::S][OlsGeom<N>
 __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ void st_stream(float2* p, float2 v) { __stcs(p, v); }
 
-template <int N, int WARPS>
+// Returns p unchanged but opaque to the optimizer, so loads through it stay where they are
+// written instead of being hoisted out of the loops.
+template <class P>
+__device__ __forceinline__ P* opaque(P* p)
+{
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
+// One forward N-point four-step DFT on the register array x (see the top of this file):
+// in:  x[n1] = u(T n1 + t)
+// out: x[n1] = U(T n1 + t)      (with n1 = s + S k', this is X(ka + E k') for ka = s T + t)
+// F1 E-point DFT, F2 twiddle, F3 transpose through buf, F4 S T-point DFTs.
+template <int N>
+__device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2* buf,
+                                              const float4* twrow, int t)
+{
+    using G = OlsGeom<N>;
+    constexpr int E = G::E, T = G::T, S = G::S, ROW = G::ROW;
+    fft_reg<E, false>(x);                                                    // F1
+    const float4* tr = opaque(twrow);
+    static_for<0, E / 2>([&](auto kh) {                                      // F2
+        constexpr int ka = 2 * decltype(kh)::value;
+        const float4 w = tr[kh];
+        if constexpr (ka != 0) x[ka] = cmul(x[ka], make_float2(w.x, w.y));
+        x[ka + 1] = cmul(x[ka + 1], make_float2(w.z, w.w));
+    });
+    static_for<0, E>([&](auto ka) { buf[decltype(ka)::value * ROW + t] = x[ka]; });   // F3
+    __syncwarp();
+    static_for<0, S>([&](auto s) {
+        constexpr int SS = decltype(s)::value;
+        const float4* row = reinterpret_cast<const float4*>(buf + (SS * T + t) * ROW);
+        float2 c[T];
+        static_for<0, T / 2>([&](auto h) {
+            const float4 q = row[h];
+            c[2 * decltype(h)::value] = make_float2(q.x, q.y);
+            c[2 * decltype(h)::value + 1] = make_float2(q.z, q.w);
+        });
+        fft_reg<T, false>(c);                                                // F4
+        static_for<0, T>([&](auto kp) { x[SS + S * decltype(kp)::value] = c[kp]; });
+    });
+    __syncwarp();
+}
+
+// The fused kernel. Each block is two passes of the same four-step DFT (which keeps the loop body
+// small enough for the instruction cache):
+//   pass 0: X = DFT(x_m)                                   (Sec. II step 1)
+//   pass 1: z = IDFT(H_R X / N) = swap(DFT(swap(H_R X / N)))  (steps 2-3), swap(a + jb) = b + ja,
+// where both swaps are free (they only choose which register holds which component). Between the
+// passes each register is scaled by its real gain g(kk) = H_R(k)/N, k = T n1 + t, kk = min(k, N-k).
+// QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
+template <int N, int WARPS, bool QOVL>
 __global__ void __launch_bounds__(WARPS * 32) ols_fp32_kernel(const OlsArgs a)
 {
     using G = OlsGeom<N>;
-    constexpr int E = G::E, T = G::T, B = G::B, S = G::S, ROW = G::ROW;
+    constexpr int E = G::E, T = G::T, B = G::B;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tw_s = reinterpret_cast<float2*>(smem_raw);
-    float* V_s = reinterpret_cast<float*>(tw_s + N);
-    const int LV = a.LV;
-    float2* bufs = reinterpret_cast<float2*>(V_s + ((LV + 3) & ~3));
-
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw_s[i] = a.tw[i];
-    for (int i = threadIdx.x; i < LV; i += blockDim.x) V_s[i] = a.V[i];
-    __syncthreads();
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bsub = lane / T, t = lane % T;
-    float2* buf = bufs + warp * G::WARP_BUF + bsub * G::BLK;
-    const int O = a.overlap, M = N - O, D = O >> 1;
+    unsigned char* wbase = smem_raw + sizeof(float2) * G::TW + (size_t)warp * G::WARP_BYTES;
+    float2* buf = reinterpret_cast<float2*>(wbase) + bsub * G::BLK;
+    float* gtab = reinterpret_cast<float*>(wbase + sizeof(float2) * B * G::BLK) + bsub * G::GT;
+    const float4* twrow = reinterpret_cast<const float4*>(tw_s + t * G::TWROW);
 
-    const int64_t warp_stride = (int64_t)gridDim.x * WARPS;
-    for (int64_t tile = (int64_t)blockIdx.x * WARPS + warp; tile < a.ntiles; tile += warp_stride) {
+    for (int i = threadIdx.x; i < G::TW / 2; i += blockDim.x)
+        reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
+    __syncthreads();
+
+    const int LV = a.LV;
+    const int O = QOVL ? N / 4 : a.overlap;
+    const int M = N - O, D = O >> 1;
+    int table_k1 = -1;   // band the gain table currently holds
+
+    // each warp takes one contiguous range of tiles, so consecutive blocks of a stream stay in
+    // one warp: the overlap samples are L2 hits and the gain table survives until the band changes
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
+    const int64_t per = a.ntiles / nwarps, extra = a.ntiles % nwarps;
+    const int64_t tile_begin = gw * per + (gw < extra ? gw : extra);
+    const int64_t tile_end = tile_begin + per + (gw < extra ? 1 : 0);
+    for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
         // ---- which job and block this lane group works on
         OlsJob job;
         int64_t blk;
@@ -125,111 +210,132 @@ __global__ void __launch_bounds__(WARPS * 32) ols_fp32_kernel(const OlsArgs a)
             for (int i = 0; i < a.nchg; ++i)
                 if (a.chg_block[i] <= blk) k1 = a.chg_band[i];
         }
+        if (!active) k1 = table_k1;
+
+        // ---- ask L2 for the samples the warp's next tile adds (the rest is this tile's span)
+        if (lane == 0 && tile + 1 < tile_end) {
+            const int64_t e = (blk + B - 1) * (int64_t)M - O + N;   // end of this tile's span
+            int64_t e2 = e + (int64_t)B * M;
+            if (e2 > nsamp) e2 = nsamp;
+            const int64_t cnt = (e2 - e) & ~int64_t(1);
+            if (e >= 0 && cnt > 0) prefetch_l2_bulk(in + e, (uint32_t)(cnt * sizeof(float2)));
+        }
+
+        // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real), Sec. III-E)
+        if (__any_sync(0xffffffffu, k1 != table_k1)) {
+            __syncwarp();
+            if (k1 >= 1) build_gains<N>(gtab, t, k1, LV, a.V);
+            table_k1 = k1;
+            __syncwarp();
+        }
 
         // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation)
         const int64_t s0 = blk * M - O;
-        float2 v[E];
+        float2 x[E];
         const bool interior = active && s0 >= 0 && s0 + N <= nsamp;
         if (__all_sync(0xffffffffu, interior)) {
             const float2* src = in + s0 + t;
-            static_for<0, E>([&](auto n1) { v[n1] = ld_stream(src + decltype(n1)::value * T); });
+            static_for<0, E>([&](auto n1) { x[n1] = ld_stream(src + decltype(n1)::value * T); });
         } else {
             static_for<0, E>([&](auto n1) {
                 const int64_t si = s0 + decltype(n1)::value * T + t;
-                float2 x = make_float2(0.f, 0.f);
+                float2 v = make_float2(0.f, 0.f);
                 if (active) {
                     if (si >= 0) {
-                        if (si < nsamp) x = ld_stream(in + si);
+                        if (si < nsamp) v = ld_stream(in + si);
                     } else if (tail_in) {
-                        x = tail_in[O + si];
+                        v = tail_in[O + si];
                     }
                 }
-                v[n1] = x;
+                x[n1] = v;
             });
         }
 
-        // ---- forward DFT (Sec. II step 1)
-        fft_reg<E, false>(v);
-        static_for<0, E>([&](auto ka) { v[ka] = cmul(v[ka], tw_s[decltype(ka)::value * T + t]); });
-        static_for<0, E>([&](auto ka) { buf[decltype(ka)::value * ROW + t] = v[ka]; });
-        __syncwarp();
-        float2 c[S][T];
-        static_for<0, S>([&](auto s) {
-            static_for<0, T>([&](auto n2) {
-                c[s][n2] = buf[(decltype(s)::value * T + t) * ROW + decltype(n2)::value];
-            });
-        });
-        __syncwarp();
-        static_for<0, S>([&](auto s) { fft_reg<T, false>(c[s]); });
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            four_step_dft<N>(x, buf, twrow, t);
+            if (pass == 0) {
+                // swap(g X): H_R(k)/N of eq. (FS_Hk_real) for k = T n1 + t (Sec. II step 2)
+                const float* lo = opaque(gtab + t);
+                const float* hi = opaque(gtab + (N - t));
+                static_for<0, E>([&](auto n1) {
+                    constexpr int N1 = decltype(n1)::value;
+                    constexpr int K = N1 * T;
+                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
+                    x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
+                });
+            }
+        }
 
-        // ---- multiply by H_R(k, b) (step 2; the phase term is the output shift below)
-        apply_band<N>(c, t, k1, LV, V_s);
-
-        // ---- inverse DFT (step 3)
-        static_for<0, S>([&](auto s) { fft_reg<T, true>(c[s]); });
-        static_for<0, S>([&](auto s) {
-            static_for<0, T>([&](auto n2) {
-                buf[(decltype(s)::value * T + t) * ROW + decltype(n2)::value] = c[s][n2];
-            });
-        });
-        __syncwarp();
-        static_for<0, E>([&](auto ka) { v[ka] = buf[decltype(ka)::value * ROW + t]; });
-        __syncwarp();
-        static_for<0, E>([&](auto ka) { v[ka] = cmul_conj(v[ka], tw_s[decltype(ka)::value * T + t]); });
-        fft_reg<E, true>(v);
-
-        // ---- discard and store (steps 4-5): z(n), n = T n1 + t, kept for D <= n < D + M
+        // ---- discard and store (steps 4-5): z(n) = swap(x[n1]), n = T n1 + t, kept for
+        //      D <= n < D + M (the exp(-j 2 pi k D / N) phase of eq. (FS_Hk_exp) as a shift)
         if (active) {
             const int64_t obase = blk * M - D;
-            static_for<0, E>([&](auto n1) {
-                const int n = decltype(n1)::value * T + t;
-                if (n >= D && n < D + M) {
-                    const int64_t oi = obase + n;
-                    if (oi < nsamp) st_stream(out + oi, v[n1]);
+            if constexpr (QOVL) {
+                // kept rows n1 in [E/8, 7E/8): every lane stores, no per-sample test when the
+                // block is complete
+                float2* dst = out + obase + t;
+                if (obase + D + M <= nsamp) {
+                    static_for<E / 8, 7 * E / 8>([&](auto n1) {
+                        st_stream(dst + decltype(n1)::value * T, make_float2(x[n1].y, x[n1].x));
+                    });
+                } else {
+                    static_for<E / 8, 7 * E / 8>([&](auto n1) {
+                        const int64_t oi = obase + decltype(n1)::value * T + t;
+                        if (oi < nsamp) st_stream(out + oi, make_float2(x[n1].y, x[n1].x));
+                    });
                 }
-            });
+            } else {
+                static_for<0, E>([&](auto n1) {
+                    const int n = decltype(n1)::value * T + t;
+                    if (n >= D && n < D + M) {
+                        const int64_t oi = obase + n;
+                        if (oi < nsamp) st_stream(out + oi, make_float2(x[n1].y, x[n1].x));
+                    }
+                });
+            }
             // the lane group of the job's last block hands the stream's last O input samples on
             if (blk == nblocks - 1 && job.tail_out) {
                 float2* tail_out = job.tail_out;
                 for (int i = t; i < O; i += T) {
                     const int64_t si = nsamp - O + i;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (si >= 0) x = in[si];
-                    else if (tail_in) x = tail_in[O + si];
-                    tail_out[i] = x;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (si >= 0) v = in[si];
+                    else if (tail_in) v = tail_in[O + si];
+                    tail_out[i] = v;
                 }
             }
         }
     }
 }
 
-// Writes the H_R(k) that apply_band<N> applies for band k1 (test hook), using the same code and
-// register layout: one lane group of T threads, spectrum of ones.
+// Writes the H_R(k) that the kernel applies for band k1 (test hook): the same table build and
+// the same load_gains indexing, one lane group of T threads; the table's 1/N is undone exactly.
 template <int N>
 __global__ void export_hr_kernel(const float* V, int LV, int k1, float* out)
 {
     using G = OlsGeom<N>;
     constexpr int E = G::E, T = G::T, S = G::S;
+    __shared__ float gtab[G::GT];
     const int t = threadIdx.x;
+    if (t < T) build_gains<N>(gtab, t, k1, LV, V);
+    __syncthreads();
     if (t >= T) return;
-    float2 c[S][T];
-    static_for<0, S>([&](auto s) {
-        static_for<0, T>([&](auto kp) { c[s][kp] = make_float2(1.f, 0.f); });
-    });
-    apply_band<N>(c, t, k1, LV, V);
+    float g[S][T];
+    load_gains<N>(g, gtab, t);
     static_for<0, S>([&](auto s) {
         static_for<0, T>([&](auto kp) {
-            out[decltype(s)::value * T + t + E * decltype(kp)::value] = c[s][kp].x;
+            out[decltype(s)::value * T + t + E * decltype(kp)::value] = g[s][kp] * (float)N;
         });
     });
 }
 
 // Launch helpers (instantiated per N in ols_fp32_n<N>.cu).
-template <int N, int WARPS>
+template <int N, int WARPS, bool QOVL>
 cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, cudaStream_t st, int* grid_out)
 {
-    const size_t smem = ols_smem_bytes<N>(WARPS, a.LV);
-    auto kern = ols_fp32_kernel<N, WARPS>;
+    const size_t smem = ols_smem_bytes<N>(WARPS);
+    auto kern = ols_fp32_kernel<N, WARPS, QOVL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -248,9 +354,12 @@ cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, cudaStream_t st, int* g
 template <int N>
 cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, cudaStream_t st, int* grid_out)
 {
+    const bool q = (a.overlap == N / 4);
     switch (warps) {
-    case 4: return launch_ols_fp32_w<N, 4>(a, sms, st, grid_out);
-    case 8: return launch_ols_fp32_w<N, 8>(a, sms, st, grid_out);
+    case 4: return q ? launch_ols_fp32_w<N, 4, true>(a, sms, st, grid_out)
+                     : launch_ols_fp32_w<N, 4, false>(a, sms, st, grid_out);
+    case 8: return q ? launch_ols_fp32_w<N, 8, true>(a, sms, st, grid_out)
+                     : launch_ols_fp32_w<N, 8, false>(a, sms, st, grid_out);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -61,18 +61,22 @@ extern "C" const char* vbw_version(void) { return "libvbw 0.1 (sm_103a)"; }
 // ------------------------------------------------------------------------------------------------
 // device-side table generation (FP64 on the GPU, rounded once to FP32)
 
-// tw[ka*T + n2] = exp(-j 2 pi (n2 ka mod N) / N) / sqrt(N): the four-step twiddle of the fused
-// kernel, with half of the IDFT's 1/N folded in (the other half is applied by the conjugate use).
-__global__ void vbw_twiddle_kernel(float2* tw, int N, int T)
+// tw[n2*(E+2) + ka] = exp(-j 2 pi (n2 ka mod N) / N) for ka < E (pad entries 0): the four-step
+// twiddle of the fused kernel, one row per thread n2.
+__global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N) return;
-    const int ka = idx / T, n2 = idx % T;
+    const int row = E + 2;
+    if (idx >= T * row) return;
+    const int n2 = idx / row, ka = idx % row;
+    if (ka >= E) {
+        tw[idx] = make_float2(0.f, 0.f);
+        return;
+    }
     const long long j = ((long long)n2 * (long long)ka) % N;
     double s, c;
     sincospi(-2.0 * (double)j / (double)N, &s, &c);
-    const double scale = 1.0 / sqrt((double)N);
-    tw[idx] = make_float2((float)(c * scale), (float)(s * scale));
+    tw[idx] = make_float2((float)c, (float)s);
 }
 
 __global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV)
@@ -155,11 +159,13 @@ static int env_int(const char* name, int dflt)
     return atoi(v);
 }
 
+// Warps per CTA for each N: the largest CTA whose register footprint still gives 16 resident
+// warps per SM (N <= 1024) or 8 (N = 2048). VBW_WARPS overrides it (4 or 8).
 static int default_warps(int N)
 {
-    (void)N;
-    const int w = env_int("VBW_WARPS", 8);
-    return (w == 4 || w == 8) ? w : 8;
+    const int w = env_int("VBW_WARPS", 0);
+    if (w == 4 || w == 8) return w;
+    return (N <= 256) ? 8 : 4;
 }
 
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int warps, int sms, cudaStream_t st)
@@ -176,6 +182,9 @@ static cudaError_t launch_fp32(int N, const OlsArgs& a, int warps, int sms, cuda
 }
 
 static int blocks_per_warp(int N) { return 32 / layout_T(N); }
+
+// entries of the per-plan twiddle table: T rows of E + 2 (see OlsGeom::TW)
+static int twiddle_entries(int N) { return layout_T(N) * (N / layout_T(N) + 2); }
 
 // ------------------------------------------------------------------------------------------------
 // plans
@@ -216,7 +225,7 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
             st = fail(VBW_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
             break;
         }
-        if (cudaMalloc(&p->d_tw, sizeof(float2) * N) != cudaSuccess ||
+        if (cudaMalloc(&p->d_tw, sizeof(float2) * twiddle_entries(N)) != cudaSuccess ||
             cudaMalloc(&p->d_V, sizeof(float) * LV) != cudaSuccess ||
             cudaMalloc(&d_Vd, sizeof(double) * LV) != cudaSuccess) {
             cudaGetLastError();
@@ -227,7 +236,8 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
             st = fail(VBW_ERR_CUDA, "V upload failed: %s", cudaGetErrorString(e));
             break;
         }
-        vbw_twiddle_kernel<<<(N + 255) / 256, 256>>>(p->d_tw, N, layout_T(N));
+        vbw_twiddle_kernel<<<(twiddle_entries(N) + 255) / 256, 256>>>(p->d_tw, N, layout_T(N),
+                                                                       N / layout_T(N));
         vbw_round_table_kernel<<<(LV + 255) / 256, 256>>>(d_Vd, p->d_V, LV);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
             st = fail(VBW_ERR_CUDA, "plan table kernels failed: %s", cudaGetErrorString(e));
