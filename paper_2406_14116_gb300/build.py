@@ -37,12 +37,17 @@ def headers() -> list[str]:
     return hs
 
 
+def env_flags() -> list[str]:
+    """Extra nvcc flags from VBW_NVCC_FLAGS (for tuning builds), e.g. -DVBW_MIN_WARPS_PER_SM=16."""
+    return os.environ.get("VBW_NVCC_FLAGS", "").split()
+
+
 def _compile(src: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers()])
-    if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
+    if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra and not env_flags():
         return obj
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *env_flags(), *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -165,7 +165,7 @@ static int default_warps(int N)
 {
     const int w = env_int("VBW_WARPS", 0);
     if (w == 4 || w == 8) return w;
-    return (N <= 256) ? 8 : 4;
+    return (N <= 1024) ? 8 : 4;
 }
 
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int warps, int sms, cudaStream_t st)

@@ -120,10 +120,11 @@ struct OlsArgs {
     int32_t nchg;         // single-job mode: inline band changes (block, band), sorted by block
     int32_t chg_band[kInlineChanges];
     int64_t chg_block[kInlineChanges];
-    const float2* tw;     // device twiddle table [ka][n2] = W_N^{n2 ka} / sqrt(N), N entries
+    const float2* tw;     // device twiddle table: row t holds W_N^{t ka}, ka < E, padded to E + 2
     const float* V;       // device transition samples, L_V floats
     int32_t overlap;
     int32_t LV;
+    int* status;          // device status word (bit flags, e.g. a bounded wait that gave up) or nullptr
 };
 
 }  // namespace vbw
