@@ -148,6 +148,32 @@ vbw_status vbw_batch_destroy(vbw_batch_t batch);
 /* Number of kernel launches the last vbw_batch_run of this batch issued (for accounting). */
 vbw_status vbw_batch_launches(vbw_batch_t batch, int* launches);
 
+/* How vbw_batch_run executes a batch whose signals use several plans:
+ *   VBW_BATCH_PER_PLAN  one persistent full-GPU launch per plan, in sequence;
+ *   VBW_BATCH_MIXED     one persistent launch over every plan with overlap N/4 and N <= 1024
+ *                       (warps switch the transform size per tile), the other plans launched
+ *                       beside it on a forked stream; mixed_share is the share of the SMs for the
+ *                       mixed launch (0 = in proportion to the transform work);
+ *   VBW_BATCH_AUTO      MIXED when at least two plans mix, else PER_PLAN (the default).
+ * Errors: VBW_ERR_INVALID_ARG. */
+enum { VBW_BATCH_AUTO = 0, VBW_BATCH_PER_PLAN = 1, VBW_BATCH_MIXED = 2 };
+vbw_status vbw_batch_set_mode(vbw_batch_t batch, int mode, double mixed_share);
+
+/* Tuning: warps per CTA (4 or 8; 0 restores the default) of the single-plan kernel for transform
+ * size N, for every later launch in this process. The autotuner (paper_2406_14116_gb300/tune.py)
+ * measures the choices and writes them to a cache that it loads through this call. */
+vbw_status vbw_tune_set(int N, int warps);
+
+/* Device status word of a plan's launches (synchronizes the device): bit 0 = a bounded device-side
+ * wait gave up (the kernel's warp stopped and its outputs are incomplete). Returns VBW_ERR_TIMEOUT
+ * when bit 0 is set. clear != 0 resets the word. */
+vbw_status vbw_plan_status(vbw_plan_t plan, int* flags, int clear);
+
+/* Test hook for the failure-detection path: flags bit 0 makes later launches mark blocks as staged
+ * without issuing their copies and shortens the device wait limit to about a millisecond, so the
+ * bounded waits run out, set the status word and stop the warp, with no fault. 0 turns it off. */
+vbw_status vbw_debug_set(int flags);
+
 /* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */
 vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);

@@ -1,23 +1,20 @@
-// Fused FP32 overlap-save VBW kernel: gather -> N-point FFT -> H_R on the fly -> IFFT -> discard
-// and store, one kernel, one pass over HBM (Sec. II steps 1-5 with eq. (FS_Hk_exp)/(FS_Hk_real)).
+// Fused FP32 overlap-save VBW kernels: gather -> N-point DFT -> H_R on the fly -> inverse DFT ->
+// discard and store, one kernel, one pass over HBM (Sec. II steps 1-5 with eq. (FS_Hk_exp) and
+// eq. (FS_Hk_real)).
 //
-// Decomposition (four-step FFT, N = E * T):
-//   thread t of a block holds x(T n1 + t), n1 = 0..E-1 (coalesced loads),
+// Four-step DFT, N = E * T, T threads per block, thread t holding x(T n1 + t) in register n1:
 //   F1  E-point register DFT over n1                      -> A(ka, t)
-//   F2  A(ka, t) *= W_N^{t ka}                            (shared-memory table; ka = 0 is 1)
+//   F2  A(ka, t) *= W_N^{t ka}                            (shared-memory row of thread t)
 //   F3  shared-memory transpose: thread t now owns ka = s T + t (s < E/T), every n2
 //   F4  T-point register DFTs over n2                     -> X(ka + E k'), k' = 0..T-1
-//   H   X(k) *= H_R(k) / N: the real gains come from a per-warp table g(kk), kk = min(k, N-k),
-//       rebuilt from (k1, L_V, V) only when the block's band differs from the table's; they are
-//       folded into the first stage of I1, so passband and stopband bins cost no extra work, and
-//       they carry the 1/N of eq. (OLS_dn) (a power of two, so the scaling is exact)
-//   I1  T-point inverse register DFTs over k'             -> B(ka, n2)
-//   I3  transpose back: thread t owns n2 = t, every ka
-//   I2  B(ka, t) *= conj(W_N^{t ka})
-//   I4  E-point inverse register DFT over ka              -> z(T n1 + t)
-// The linear phase exp(-j 2 pi k D / N), D = O/2, of eq. (FS_Hk_exp) is an exact circular shift of
-// the IDFT output by D samples, so nothing multiplies it: the kept outputs w(O..N-1) of Sec. II
-// step 4 are z(D..D+M-1), written to y(mM .. mM+M-1).
+// With n1 = s + (E/T) k' the output index ka + E k' equals T n1 + t: the output layout is the
+// input layout. So the inverse DFT reuses the same four steps through
+// IDFT(y) = swap(DFT(swap(y))), swap(a + jb) = b + ja, whose swaps are register renaming.
+// Between the two passes each register is scaled by its real gain g = H_R(k)/N (k = T n1 + t),
+// read from a per-warp table rebuilt only when the band changes; 1/N (eq. (OLS_dn)) is a power of
+// two, so the scaling is exact. The linear phase exp(-j 2 pi k D / N), D = O/2, of eq. (FS_Hk_exp)
+// is an exact circular shift of the inverse output by D samples: the kept outputs w(O..N-1) of
+// Sec. II step 4 are z(D..D+M-1), written to y(mM .. mM+M-1).
 #pragma once
 
 #include "fft_reg.cuh"
@@ -45,9 +42,10 @@ struct OlsGeom {
     static constexpr int GT_MIN = N / 2 + 1;
     static constexpr int GT = (B == 1) ? ((GT_MIN + 3) & ~3)
                                        : GT_MIN + ((T - GT_MIN % 32) % 32 + 32) % 32;
-    // per warp: B transpose buffers, B gain tables, B mbarriers (8 bytes each)
-    static constexpr size_t BAR_OFF = (sizeof(float2) * B * BLK + sizeof(float) * B * GT + 7) / 8 * 8;
-    static constexpr size_t WARP_BYTES = (BAR_OFF + 8 * B + 15) / 16 * 16;
+    // per warp: kMaxGroups mbarriers (fixed place for every N), B transpose buffers, B gain tables
+    static constexpr size_t BUF_OFF = 32;
+    static constexpr size_t GAIN_OFF = BUF_OFF + sizeof(float2) * B * BLK;
+    static constexpr size_t WARP_BYTES = (GAIN_OFF + sizeof(float) * B * GT + 15) / 16 * 16;
     static_assert(E * T == N && E % T == 0, "layout must satisfy N = E*T with T | E");
     static_assert(BLK % 2 == 0 && T % 2 == 0, "transpose rows must stay 16-byte aligned");
 };
@@ -227,211 +225,312 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
 #define VBW_OLS_BOUNDS(W) __launch_bounds__((W) * 32)
 #endif
 
-// The job and block of lane group bsub in warp-tile `tile`. The descriptors are re-read through
-// opaque pointers (L1 hits) wherever they are needed, so none of their fields stays live in
-// registers across the DFT passes.
-template <int B>
-__device__ __forceinline__ void job_of(const OlsArgs& a, int64_t tile, int bsub, OlsJob& job, int64_t& blk)
-{
-    if (a.jobs) {
-        const int2 td = opaque(a.tiles)[tile];
-        job = opaque(a.jobs)[td.x];
-        blk = (int64_t)td.y + bsub;
-    } else {
+constexpr int kMaxGroups = 4;   // blocks per warp for the smallest N (T = 8)
+
+// Job sources. The descriptors are re-read through opaque pointers (L1 hits) wherever they are
+// needed, so none of their fields stays live in registers across the DFT passes.
+struct SingleJobSource {        // one stream segment held in the kernel parameters
+    const OlsArgs& a;
+    template <int B>
+    __device__ __forceinline__ void get(int64_t tile, int bsub, OlsJob& job, int64_t& blk) const
+    {
         job = a.job;
         blk = tile * B + bsub;
     }
-}
+    __device__ __forceinline__ int band(const OlsJob& job, int64_t blk, bool) const
+    {
+        int k1 = job.band0;
+        for (int i = 0; i < a.nchg; ++i)
+            if (a.chg_block[i] <= blk) k1 = a.chg_band[i];
+        return k1;
+    }
+};
 
-// The fused kernel. Each block is two passes of the same four-step DFT (which keeps the loop body
-// small enough for the instruction cache):
-//   pass 0: X = DFT(x_m)                                   (Sec. II step 1)
-//   pass 1: z = IDFT(H_R X / N) = swap(DFT(swap(H_R X / N)))  (steps 2-3), swap(a + jb) = b + ja,
-// where both swaps are free (they only choose which register holds which component). Between the
-// passes each register is scaled by its real gain g(kk) = H_R(k)/N, k = T n1 + t, kk = min(k, N-k).
-// QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
-template <int N, int WARPS, bool QOVL>
-__global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
+struct JobListSource {          // device job array + warp-tile list (batches)
+    const OlsJob* jobs;
+    const int2* tiles;
+    template <int B>
+    __device__ __forceinline__ void get(int64_t tile, int bsub, OlsJob& job, int64_t& blk) const
+    {
+        const int2 td = opaque(tiles)[tile];
+        job = opaque(jobs)[td.x];
+        blk = (int64_t)td.y + bsub;
+    }
+    __device__ __forceinline__ int band(const OlsJob& job, int64_t blk, bool active) const
+    {
+        return (job.band && active) ? job.band[blk] : job.band0;
+    }
+};
+
+// State a warp carries from one tile to the next.
+struct WarpState {
+    int table_key;        // (plan << 16) | k1 of this lane group's gain table; -1 = none
+    bool staged;          // this lane group's next block was requested into its buffer by TMA
+    uint32_t phase_mask;  // bit g: parity of the next completion of mbarrier g (warp-uniform)
+};
+
+// One warp-tile: 32/T blocks of plan `plan`, transform size N. Returns false if the warp has to
+// stop (a staged copy never arrived; the status word says so).
+struct TileCtl {
+    int* status;          // device status word
+    long long wait_limit; // bounded-wait limit in SM cycles
+    int debug;            // bit 0: mark blocks staged without issuing the copies (test hook)
+};
+
+template <int N, bool QOVL, class Src>
+__device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_next, int plan,
+                                         const float2* tw_plan, const float* V, int LV, int O_rt,
+                                         unsigned char* wbase, int lane, WarpState& ws,
+                                         const TileCtl& ctl)
 {
     using G = OlsGeom<N>;
     constexpr int E = G::E, T = G::T, B = G::B;
+    const int bsub = lane / T, t = lane % T;
+    float2* buf = reinterpret_cast<float2*>(wbase + G::BUF_OFF) + bsub * G::BLK;
+    float* gtab = reinterpret_cast<float*>(wbase + G::GAIN_OFF) + bsub * G::GT;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase) + bsub;
+    const float4* twrow = reinterpret_cast<const float4*>(tw_plan + t * G::TWROW);
+    const int O = QOVL ? N / 4 : O_rt;
+    const int M = N - O, D = O >> 1;
 
+    float2 x[E];
+    {
+        // ---- which job and block this lane group works on, and its band
+        OlsJob job;
+        int64_t blk;
+        src.template get<B>(tile, bsub, job, blk);
+        const int64_t nsamp = job.nsamp;
+        const bool active = blk * M < nsamp;
+        const int k1 = src.band(job, blk, active);
+        const int key = active ? ((plan << 16) | k1) : ws.table_key;
+
+        // ---- ask L2 for the samples the warp's next tile adds (the rest is this span)
+        if (lane == 0 && has_next) {
+            const int64_t e = (blk + B - 1) * (int64_t)M - O + N;
+            int64_t e2 = e + (int64_t)B * M;
+            if (e2 > nsamp) e2 = nsamp;
+            const int64_t cnt = (e2 - e) & ~int64_t(1);
+            if (e >= 0 && cnt > 0) prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+        }
+
+        // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
+        if (__any_sync(0xffffffffu, key != ws.table_key)) {
+            __syncwarp();
+            if (active) build_gains<N>(gtab, t, k1, LV, V);
+            ws.table_key = key;
+            __syncwarp();
+        }
+
+        // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation): from the TMA
+        //      staging copy when the previous tile requested it, else from global memory
+        const int64_t s0 = blk * M - O;
+        const bool interior = active && s0 >= 0 && s0 + N <= nsamp;
+        uint32_t groups = 0;    // lane groups whose block was staged (warp-uniform)
+        {
+            const uint32_t leaders = __ballot_sync(0xffffffffu, ws.staged && t == 0);
+            static_for<0, B>([&](auto g) {
+                if ((leaders >> (decltype(g)::value * T)) & 1u) groups |= 1u << decltype(g)::value;
+            });
+        }
+        bool have = false, lost = false;
+        if (ws.staged) {
+            const uint32_t parity = (ws.phase_mask >> bsub) & 1u;
+            have = mbar_wait_bounded(bar, parity, ctl.wait_limit);
+            if (!have) {
+                // flag it, then wait once more for the copy that may still be in flight
+                if (t == 0 && ctl.status) atomicOr(ctl.status, kStatusTmaTimeout);
+                have = mbar_wait_bounded(bar, parity, ctl.wait_limit);
+                lost = !have;
+            }
+            ws.staged = false;
+        }
+        ws.phase_mask ^= groups;
+        if (__any_sync(0xffffffffu, lost)) return false;
+        if (__all_sync(0xffffffffu, have)) {
+            static_for<0, E>([&](auto n1) { x[n1] = buf[decltype(n1)::value * T + t]; });
+        } else if (__all_sync(0xffffffffu, interior)) {
+            const float2* sp = job.in + s0 + t;
+            static_for<0, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
+        } else {
+            static_for<0, E>([&](auto n1) {
+                const int64_t si = s0 + decltype(n1)::value * T + t;
+                float2 v = make_float2(0.f, 0.f);
+                if (active) {
+                    if (si >= 0) {
+                        if (si < nsamp) v = ld_stream(job.in + si);
+                    } else if (job.tail_in) {
+                        v = job.tail_in[O + si];
+                    }
+                }
+                x[n1] = v;
+            });
+        }
+    }
+
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        four_step_dft<N>(x, buf, twrow, t, [&]() {
+#if VBW_TMA_STAGE
+            if (pass != 1 || !has_next) return;
+            // the lane group's next block (same plan only): TMA-staged when its span is interior
+            OlsJob nj;
+            int64_t nb;
+            src.template get<B>(tile + 1, bsub, nj, nb);
+            const int64_t ns0 = nb * M - O;
+            if (nj.plan == plan && ns0 >= 0 && ns0 + N <= nj.nsamp &&
+                (reinterpret_cast<uintptr_t>(nj.in + ns0) & 15) == 0) {
+                if (t == 0 && !(ctl.debug & 1)) {
+                    fence_proxy_async_smem();
+                    tma_load_span(buf, nj.in + ns0, (uint32_t)(N * sizeof(float2)), bar);
+                }
+                ws.staged = true;
+            }
+#endif
+        });
+        if (pass == 0) {
+            // swap(g X): H_R(k)/N of eq. (FS_Hk_real) for k = T n1 + t (Sec. II step 2)
+            const float* lo = opaque(gtab + t);
+            const float* hi = opaque(gtab + (N - t));
+            static_for<0, E>([&](auto n1) {
+                constexpr int N1 = decltype(n1)::value;
+                constexpr int K = N1 * T;
+                const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
+                x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
+            });
+        }
+    }
+
+    // ---- discard and store (steps 4-5): z(n) = swap(x[n1]), n = T n1 + t, kept for
+    //      D <= n < D + M (the exp(-j 2 pi k D / N) phase of eq. (FS_Hk_exp) as a shift)
+    OlsJob job;
+    int64_t blk;
+    src.template get<B>(tile, bsub, job, blk);
+    const int64_t nsamp = job.nsamp;
+    if (blk * M < nsamp) {
+        const int64_t obase = blk * M - D;
+        if constexpr (QOVL) {
+            // kept rows n1 in [E/8, 7E/8): every lane stores, no per-sample test when the block
+            // is complete
+            float2* dst = job.out + obase + t;
+            if (obase + D + M <= nsamp) {
+                static_for<E / 8, 7 * E / 8>([&](auto n1) {
+                    st_stream(dst + decltype(n1)::value * T, make_float2(x[n1].y, x[n1].x));
+                });
+            } else {
+                static_for<E / 8, 7 * E / 8>([&](auto n1) {
+                    const int64_t oi = obase + decltype(n1)::value * T + t;
+                    if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
+                });
+            }
+        } else {
+            static_for<0, E>([&](auto n1) {
+                const int n = decltype(n1)::value * T + t;
+                if (n >= D && n < D + M) {
+                    const int64_t oi = obase + n;
+                    if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
+                }
+            });
+        }
+        // the lane group of the job's last block hands the stream's last O input samples on
+        if ((blk + 1) * M >= nsamp && job.tail_out) {
+            for (int i = t; i < O; i += T) {
+                const int64_t si = nsamp - O + i;
+                float2 v = make_float2(0.f, 0.f);
+                if (si >= 0) v = job.in[si];
+                else if (job.tail_in) v = job.tail_in[O + si];
+                job.tail_out[i] = v;
+            }
+        }
+    }
+    return true;
+}
+
+// Contiguous range of warp-tiles of warp gw out of nwarps.
+__device__ __forceinline__ void warp_range(int64_t ntiles, int64_t nwarps, int64_t gw, int64_t& b, int64_t& e)
+{
+    const int64_t per = ntiles / nwarps, extra = ntiles % nwarps;
+    b = gw * per + (gw < extra ? gw : extra);
+    e = b + per + (gw < extra ? 1 : 0);
+}
+
+// Single-plan kernel: every tile has the same N (one stream, or a batch grouped by plan).
+// Each warp takes one contiguous range of tiles, so consecutive blocks of a stream stay in one
+// warp: the overlap samples are L2 hits and the gain table survives until the band changes.
+// QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
+template <int N, int WARPS, bool QOVL, bool BATCH>
+__global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
+{
+    using G = OlsGeom<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tw_s = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bsub = lane / T, t = lane % T;
     unsigned char* wbase = smem_raw + sizeof(float2) * G::TW + (size_t)warp * G::WARP_BYTES;
-    float2* buf = reinterpret_cast<float2*>(wbase) + bsub * G::BLK;
-    float* gtab = reinterpret_cast<float*>(wbase + sizeof(float2) * B * G::BLK) + bsub * G::GT;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + G::BAR_OFF) + bsub;
-    const float4* twrow = reinterpret_cast<const float4*>(tw_s + t * G::TWROW);
 
     for (int i = threadIdx.x; i < G::TW / 2; i += blockDim.x)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
-    if (t == 0) mbar_init(bar, 1);
+    if (lane < kMaxGroups) mbar_init(reinterpret_cast<uint64_t*>(wbase) + lane, 1);
     __syncthreads();
 
-    const int O = QOVL ? N / 4 : a.overlap;
-    const int M = N - O, D = O >> 1;
-    int table_k1 = -1;      // band the gain table currently holds
-    bool staged = false;    // this lane group's current block was requested into buf by TMA
-    uint32_t phase = 0;     // mbarrier phase that staged copy completes
+    WarpState ws{-1, false, 0u};
+    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug};
+    int64_t tb, te;
+    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
+    for (int64_t tile = tb; tile < te; ++tile) {
+        bool ok;
+        if constexpr (BATCH)
+            ok = ols_tile<N, QOVL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0, tw_s, a.V,
+                                   a.LV, a.overlap, wbase, lane, ws, ctl);
+        else
+            ok = ols_tile<N, QOVL>(SingleJobSource{a}, tile, tile + 1 < te, 0, tw_s, a.V, a.LV,
+                                   a.overlap, wbase, lane, ws, ctl);
+        if (!ok) return;
+    }
+}
 
-    // each warp takes one contiguous range of tiles, so consecutive blocks of a stream stay in
-    // one warp: the overlap samples are L2 hits and the gain table survives until the band changes
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
-    const int64_t per = a.ntiles / nwarps, extra = a.ntiles % nwarps;
-    const int64_t tile_begin = gw * per + (gw < extra ? gw : extra);
-    const int64_t tile_end = tile_begin + per + (gw < extra ? 1 : 0);
-    for (int64_t tile = tile_begin; tile < tile_end; ++tile) {
-        float2 x[E];
-        {
-            // ---- which job and block this lane group works on, and its band
-            OlsJob job;
-            int64_t blk;
-            job_of<B>(a, tile, bsub, job, blk);
-            const int64_t nsamp = job.nsamp;
-            const bool active = blk * M < nsamp;
-            int k1 = job.band0;
-            if (job.band) {
-                if (active) k1 = job.band[blk];
-            } else {
-                for (int i = 0; i < a.nchg; ++i)
-                    if (a.chg_block[i] <= blk) k1 = a.chg_band[i];
-            }
-            if (!active) k1 = table_k1;
+// Mixed-plan persistent kernel: one launch over a tile list whose jobs use different plans with
+// N <= MAXN and overlap N/4. Every plan's twiddle rows sit in shared memory; a warp switches the
+// transform size per tile (jobs are grouped by plan, so a warp's contiguous range crosses few
+// plan boundaries).
+template <int MAXN, int WARPS>
+__global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int p = 0; p < a.nplans; ++p) {
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float2*>(smem_raw) + a.plans[p].tw_off);
+        const float4* srcp = reinterpret_cast<const float4*>(a.plans[p].tw);
+        for (int i = threadIdx.x; i < a.plans[p].tw_len / 2; i += blockDim.x) dst[i] = srcp[i];
+    }
+    unsigned char* wbase = smem_raw + a.tw_bytes + (size_t)warp * a.warp_bytes;
+    if (lane < kMaxGroups) mbar_init(reinterpret_cast<uint64_t*>(wbase) + lane, 1);
+    __syncthreads();
 
-            // ---- ask L2 for the samples the warp's next tile adds (the rest is this span)
-            if (lane == 0 && tile + 1 < tile_end) {
-                const int64_t e = (blk + B - 1) * (int64_t)M - O + N;
-                int64_t e2 = e + (int64_t)B * M;
-                if (e2 > nsamp) e2 = nsamp;
-                const int64_t cnt = (e2 - e) & ~int64_t(1);
-                if (e >= 0 && cnt > 0) prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+    const JobListSource src{a.jobs, a.tiles};
+    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug};
+    WarpState ws{-1, false, 0u};
+    int64_t tb, te;
+    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
+    for (int64_t tile = tb; tile < te; ++tile) {
+        const int2 td = opaque(a.tiles)[tile];
+        const int plan = opaque(a.jobs)[td.x].plan;
+        const MixedPlan& P = a.plans[plan];
+        const float2* tw = reinterpret_cast<const float2*>(smem_raw) + P.tw_off;
+        const bool nx = tile + 1 < te;
+        bool ok = true;
+        switch (P.N) {
+        case 128: ok = ols_tile<128, true>(src, tile, nx, plan, tw, P.V, P.LV, 32, wbase, lane, ws, ctl); break;
+        case 256: ok = ols_tile<256, true>(src, tile, nx, plan, tw, P.V, P.LV, 64, wbase, lane, ws, ctl); break;
+        case 512: ok = ols_tile<512, true>(src, tile, nx, plan, tw, P.V, P.LV, 128, wbase, lane, ws, ctl); break;
+        default:
+            if constexpr (MAXN >= 1024) {
+                if (P.N == 1024) { ok = ols_tile<1024, true>(src, tile, nx, plan, tw, P.V, P.LV, 256, wbase, lane, ws, ctl); break; }
             }
-
-            // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
-            if (__any_sync(0xffffffffu, k1 != table_k1)) {
-                __syncwarp();
-                if (k1 >= 1) build_gains<N>(gtab, t, k1, a.LV, a.V);
-                table_k1 = k1;
-                __syncwarp();
+            if constexpr (MAXN >= 2048) {
+                if (P.N == 2048) { ok = ols_tile<2048, true>(src, tile, nx, plan, tw, P.V, P.LV, 512, wbase, lane, ws, ctl); break; }
             }
-
-            // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation): from
-            //      the TMA staging copy when the previous block requested it, else from global
-            const int64_t s0 = blk * M - O;
-            const bool interior = active && s0 >= 0 && s0 + N <= nsamp;
-            bool have = false, lost = false;
-            if (staged) {
-                have = mbar_wait_bounded(bar, phase, kWaitLimitCycles);
-                if (!have) {
-                    // flag it, then wait once more for the copy that may still be in flight
-                    if (t == 0 && a.status) atomicOr(a.status, kStatusTmaTimeout);
-                    have = mbar_wait_bounded(bar, phase, kWaitLimitCycles);
-                    lost = !have;
-                }
-                if (have) phase ^= 1u;
-                staged = false;
-            }
-            if (__any_sync(0xffffffffu, lost)) return;   // the warp stops; the host sees the flag
-            if (__all_sync(0xffffffffu, have)) {
-                static_for<0, E>([&](auto n1) { x[n1] = buf[decltype(n1)::value * T + t]; });
-            } else if (__all_sync(0xffffffffu, interior)) {
-                const float2* src = job.in + s0 + t;
-                static_for<0, E>([&](auto n1) { x[n1] = ld_stream(src + decltype(n1)::value * T); });
-            } else {
-                static_for<0, E>([&](auto n1) {
-                    const int64_t si = s0 + decltype(n1)::value * T + t;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (active) {
-                        if (si >= 0) {
-                            if (si < nsamp) v = ld_stream(job.in + si);
-                        } else if (job.tail_in) {
-                            v = job.tail_in[O + si];
-                        }
-                    }
-                    x[n1] = v;
-                });
-            }
+            break;
         }
-
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            four_step_dft<N>(x, buf, twrow, t, [&]() {
-#if VBW_TMA_STAGE
-                if (pass != 1 || tile + 1 >= tile_end) return;
-                // the lane group's next block: TMA-staged into buf when its span is interior
-                OlsJob nj;
-                int64_t nb;
-                job_of<B>(a, tile + 1, bsub, nj, nb);
-                const int64_t ns0 = nb * M - O;
-                if (ns0 >= 0 && ns0 + N <= nj.nsamp &&
-                    (reinterpret_cast<uintptr_t>(nj.in + ns0) & 15) == 0) {
-                    if (t == 0) {
-                        fence_proxy_async_smem();
-                        tma_load_span(buf, nj.in + ns0, (uint32_t)(N * sizeof(float2)), bar);
-                    }
-                    staged = true;
-                }
-#endif
-            });
-            if (pass == 0) {
-                // swap(g X): H_R(k)/N of eq. (FS_Hk_real) for k = T n1 + t (Sec. II step 2)
-                const float* lo = opaque(gtab + t);
-                const float* hi = opaque(gtab + (N - t));
-                static_for<0, E>([&](auto n1) {
-                    constexpr int N1 = decltype(n1)::value;
-                    constexpr int K = N1 * T;
-                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
-                    x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
-                });
-            }
-        }
-
-        // ---- discard and store (steps 4-5): z(n) = swap(x[n1]), n = T n1 + t, kept for
-        //      D <= n < D + M (the exp(-j 2 pi k D / N) phase of eq. (FS_Hk_exp) as a shift)
-        OlsJob job;
-        int64_t blk;
-        job_of<B>(a, tile, bsub, job, blk);
-        const int64_t nsamp = job.nsamp;
-        if (blk * M < nsamp) {
-            const int64_t obase = blk * M - D;
-            if constexpr (QOVL) {
-                // kept rows n1 in [E/8, 7E/8): every lane stores, no per-sample test when the
-                // block is complete
-                float2* dst = job.out + obase + t;
-                if (obase + D + M <= nsamp) {
-                    static_for<E / 8, 7 * E / 8>([&](auto n1) {
-                        st_stream(dst + decltype(n1)::value * T, make_float2(x[n1].y, x[n1].x));
-                    });
-                } else {
-                    static_for<E / 8, 7 * E / 8>([&](auto n1) {
-                        const int64_t oi = obase + decltype(n1)::value * T + t;
-                        if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
-                    });
-                }
-            } else {
-                static_for<0, E>([&](auto n1) {
-                    const int n = decltype(n1)::value * T + t;
-                    if (n >= D && n < D + M) {
-                        const int64_t oi = obase + n;
-                        if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
-                    }
-                });
-            }
-            // the lane group of the job's last block hands the stream's last O input samples on
-            if ((blk + 1) * M >= nsamp && job.tail_out) {
-                for (int i = t; i < O; i += T) {
-                    const int64_t si = nsamp - O + i;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (si >= 0) v = job.in[si];
-                    else if (job.tail_in) v = job.tail_in[O + si];
-                    job.tail_out[i] = v;
-                }
-            }
-        }
+        if (!ok) return;
     }
 }
 
@@ -457,35 +556,47 @@ __global__ void export_hr_kernel(const float* V, int LV, int k1, float* out)
 }
 
 // Launch helpers (instantiated per N in ols_fp32_n<N>.cu).
-template <int N, int WARPS, bool QOVL>
-cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, cudaStream_t st, int* grid_out)
+template <class Kern>
+cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles, int sms, int max_ctas,
+                              cudaStream_t st, int* grid_out, const void* arg_ptr)
 {
-    const size_t smem = ols_smem_bytes<N>(WARPS);
-    auto kern = ols_fp32_kernel<N, WARPS, QOVL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int64_t ctas_needed = (a.ntiles + WARPS - 1) / WARPS;
-    const int64_t cap = (int64_t)per_sm * sms;
+    const int64_t ctas_needed = (ntiles + warps - 1) / warps;
+    int64_t cap = (int64_t)per_sm * sms;
+    if (max_ctas > 0 && cap > max_ctas) cap = max_ctas;
     const int grid = (int)(ctas_needed < cap ? ctas_needed : cap);
     if (grid_out) *grid_out = grid;
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    void* args[] = {const_cast<void*>(arg_ptr)};
+    return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(warps * 32), args, smem, st);
+}
+
+template <int N, int WARPS, bool QOVL, bool BATCH>
+cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out)
+{
+    return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
+                             a.ntiles, sms, max_ctas, st, grid_out, &a);
 }
 
 template <int N>
-cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, cudaStream_t st, int* grid_out)
+cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
     const bool q = (a.overlap == N / 4);
+    const bool b = (a.jobs != nullptr);
+    if (!q) {   // any other even overlap: runtime geometry, 4 warps per CTA
+        return b ? launch_ols_fp32_w<N, 4, false, true>(a, sms, max_ctas, st, grid_out)
+                 : launch_ols_fp32_w<N, 4, false, false>(a, sms, max_ctas, st, grid_out);
+    }
     switch (warps) {
-    case 4: return q ? launch_ols_fp32_w<N, 4, true>(a, sms, st, grid_out)
-                     : launch_ols_fp32_w<N, 4, false>(a, sms, st, grid_out);
-    case 8: return q ? launch_ols_fp32_w<N, 8, true>(a, sms, st, grid_out)
-                     : launch_ols_fp32_w<N, 8, false>(a, sms, st, grid_out);
+    case 4: return b ? launch_ols_fp32_w<N, 4, true, true>(a, sms, max_ctas, st, grid_out)
+                     : launch_ols_fp32_w<N, 4, true, false>(a, sms, max_ctas, st, grid_out);
+    case 8: return b ? launch_ols_fp32_w<N, 8, true, true>(a, sms, max_ctas, st, grid_out)
+                     : launch_ols_fp32_w<N, 8, true, false>(a, sms, max_ctas, st, grid_out);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -497,8 +608,8 @@ cudaError_t launch_export_hr(const float* V, int LV, int k1, float* out, cudaStr
     return cudaGetLastError();
 }
 
-#define VBW_INSTANTIATE_OLS(N)                                                                 \
-    template cudaError_t launch_ols_fp32<N>(const OlsArgs&, int, int, cudaStream_t, int*);     \
+#define VBW_INSTANTIATE_OLS(N)                                                                   \
+    template cudaError_t launch_ols_fp32<N>(const OlsArgs&, int, int, int, cudaStream_t, int*);  \
     template cudaError_t launch_export_hr<N>(const float*, int, int, float*, cudaStream_t);
 
 }  // namespace vbw

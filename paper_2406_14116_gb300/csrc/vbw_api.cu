@@ -19,9 +19,13 @@
 
 namespace vbw {
 template <int N>
-cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, cudaStream_t st, int* grid_out);
+cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
+                            int* grid_out);
 template <int N>
 cudaError_t launch_export_hr(const float* V, int LV, int k1, float* out, cudaStream_t st);
+cudaError_t launch_ols_mixed(const MixedArgs& a, int maxn, int warps, int sms, int max_ctas,
+                             cudaStream_t st, int* grid_out);
+size_t ols_warp_bytes(int N);
 }  // namespace vbw
 
 using namespace vbw;
@@ -91,10 +95,10 @@ __global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV)
 struct vbw_plan_s {
     int N = 0, O = 0, M = 0, LV = 0, prec = 0;
     int device = 0, sms = 0;
-    int warps = 8;
     std::vector<double> V;
     float2* d_tw = nullptr;
     float* d_V = nullptr;
+    int* d_status = nullptr;   // device status word of this plan's launches (bit flags)
 };
 
 struct vbw_stream_s {
@@ -119,6 +123,7 @@ struct BatchGroup {
     OlsJob* d_jobs = nullptr;
     int2* d_tiles = nullptr;
     int64_t ntiles = 0;
+    double cost = 0;                // transform work of the group (blocks x N log2 N)
     std::vector<int> sig;           // signal index of each job
     std::vector<int64_t> tile_off;  // first tile of each job (size jobs + 1)
 };
@@ -128,9 +133,38 @@ struct vbw_batch_s {
     std::vector<vbw_signal> sigs;
     int32_t* d_bands = nullptr;
     int last_launches = 0;
+    // mixed-plan launch over the groups that qualify (overlap N/4, N <= 1024)
+    std::vector<int> mixed_groups;
+    OlsJob* d_mjobs = nullptr;
+    int2* d_mtiles = nullptr;
+    MixedArgs margs;
+    double mixed_cost = 0;
+    int mode = VBW_BATCH_AUTO;
+    double split = 0;               // share of the SMs for the mixed launch (0 = by cost)
+    cudaStream_t s_side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_start = nullptr, ev_h = nullptr, ev_c = nullptr, ev_done = nullptr;
 };
+
+// ------------------------------------------------------------------------------------------------
+// process-wide tuning (CTA shapes), from vbw_tune_set or a tune cache
+
+static std::mutex g_tune_mu;
+static int g_tune_warps[5] = {0, 0, 0, 0, 0};   // N = 128 << i; 0 = default
+static int g_wait_limit_debug = 0;               // test hook: skip staging copies, short waits
+
+static int n_index(int N)
+{
+    switch (N) {
+    case 128: return 0;
+    case 256: return 1;
+    case 512: return 2;
+    case 1024: return 3;
+    case 2048: return 4;
+    default: return -1;
+    }
+}
 
 // ------------------------------------------------------------------------------------------------
 // validation helpers (pure host logic: no CUDA call before the arguments are known to be valid)
@@ -159,26 +193,45 @@ static int env_int(const char* name, int dflt)
     return atoi(v);
 }
 
-// Warps per CTA for each N: the largest CTA whose register footprint still gives 16 resident
-// warps per SM (N <= 1024) or 8 (N = 2048). VBW_WARPS overrides it (4 or 8).
-static int default_warps(int N)
+// Warps per CTA for each N: a tuned value (vbw_tune_set / tune cache), else VBW_WARPS (4 or 8),
+// else the largest CTA whose register footprint keeps 16 resident warps per SM (N <= 1024) or
+// 8 (N = 2048).
+static int warps_for(int N)
 {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        const int i = n_index(N);
+        if (i >= 0 && (g_tune_warps[i] == 4 || g_tune_warps[i] == 8)) return g_tune_warps[i];
+    }
     const int w = env_int("VBW_WARPS", 0);
     if (w == 4 || w == 8) return w;
     return (N <= 1024) ? 8 : 4;
 }
 
-static cudaError_t launch_fp32(int N, const OlsArgs& a, int warps, int sms, cudaStream_t st)
+static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st, int max_ctas = 0)
 {
     int grid = 0;
+    const int warps = warps_for(N);
     switch (N) {
-    case 128: return launch_ols_fp32<128>(a, warps, sms, st, &grid);
-    case 256: return launch_ols_fp32<256>(a, warps, sms, st, &grid);
-    case 512: return launch_ols_fp32<512>(a, warps, sms, st, &grid);
-    case 1024: return launch_ols_fp32<1024>(a, warps, sms, st, &grid);
-    case 2048: return launch_ols_fp32<2048>(a, warps, sms, st, &grid);
+    case 128: return launch_ols_fp32<128>(a, warps, sms, max_ctas, st, &grid);
+    case 256: return launch_ols_fp32<256>(a, warps, sms, max_ctas, st, &grid);
+    case 512: return launch_ols_fp32<512>(a, warps, sms, max_ctas, st, &grid);
+    case 1024: return launch_ols_fp32<1024>(a, warps, sms, max_ctas, st, &grid);
+    case 2048: return launch_ols_fp32<2048>(a, warps, sms, max_ctas, st, &grid);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Kernel arguments common to every launch of plan p.
+static void fill_plan_args(OlsArgs& a, const vbw_plan_s* p)
+{
+    a.tw = p->d_tw;
+    a.V = p->d_V;
+    a.overlap = p->O;
+    a.LV = p->LV;
+    a.status = p->d_status;
+    a.wait_limit = g_wait_limit_debug ? 2000000LL : 0;
+    a.debug = g_wait_limit_debug ? 1 : 0;
 }
 
 static int blocks_per_warp(int N) { return 32 / layout_T(N); }
@@ -214,7 +267,6 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
     p->LV = LV;
     p->prec = precision;
     p->V.assign(V, V + LV);
-    p->warps = default_warps(N);
     vbw_status st = VBW_OK;
     double* d_Vd = nullptr;
     do {
@@ -227,12 +279,14 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
         }
         if (cudaMalloc(&p->d_tw, sizeof(float2) * twiddle_entries(N)) != cudaSuccess ||
             cudaMalloc(&p->d_V, sizeof(float) * LV) != cudaSuccess ||
+            cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&d_Vd, sizeof(double) * LV) != cudaSuccess) {
             cudaGetLastError();
             st = fail(VBW_ERR_NOMEM, "device allocation for the plan failed");
             break;
         }
-        if ((e = cudaMemcpy(d_Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        if ((e = cudaMemcpy(d_Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) {
             st = fail(VBW_ERR_CUDA, "V upload failed: %s", cudaGetErrorString(e));
             break;
         }
@@ -248,6 +302,7 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
     if (st != VBW_OK) {
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_V) cudaFree(p->d_V);
+        if (p->d_status) cudaFree(p->d_status);
         delete p;
         return st;
     }
@@ -260,7 +315,34 @@ extern "C" vbw_status vbw_plan_destroy(vbw_plan_t p)
     if (!p) return fail(VBW_ERR_INVALID_ARG, "plan is NULL");
     cudaFree(p->d_tw);
     cudaFree(p->d_V);
+    cudaFree(p->d_status);
     delete p;
+    return ok();
+}
+
+extern "C" vbw_status vbw_plan_status(vbw_plan_t p, int* flags, int clear)
+{
+    if (!p || !flags) return fail(VBW_ERR_INVALID_ARG, "NULL argument");
+    VBW_CUDA(cudaMemcpy(flags, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear) VBW_CUDA(cudaMemset(p->d_status, 0, sizeof(int)));
+    if (*flags & 1) return fail(VBW_ERR_TIMEOUT, "a bounded device wait gave up (status 0x%x)", *flags);
+    return ok();
+}
+
+extern "C" vbw_status vbw_tune_set(int N, int warps)
+{
+    const int i = n_index(N);
+    if (i < 0) return fail(VBW_ERR_INVALID_ARG, "N=%d is not a supported transform size", N);
+    if (warps != 0 && warps != 4 && warps != 8)
+        return fail(VBW_ERR_INVALID_ARG, "warps=%d: must be 0 (default), 4 or 8", warps);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_warps[i] = warps;
+    return ok();
+}
+
+extern "C" vbw_status vbw_debug_set(int flags)
+{
+    g_wait_limit_debug = flags & 1;
     return ok();
 }
 
@@ -409,11 +491,8 @@ static vbw_status launch_stream_range(vbw_stream_s* s, const float2* in, float2*
     a.nchg = nchg;
     const int B = blocks_per_warp(p->N);
     a.ntiles = (nb + B - 1) / B;
-    a.tw = p->d_tw;
-    a.V = p->d_V;
-    a.overlap = p->O;
-    a.LV = p->LV;
-    cudaError_t e = launch_fp32(p->N, a, p->warps, p->sms, s->st);
+    fill_plan_args(a, p);
+    cudaError_t e = launch_fp32(p->N, a, p->sms, s->st);
     if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "filter launch failed: %s", cudaGetErrorString(e));
     if (keep_tail) s->cur ^= 1;
     s->pos += nb;
@@ -618,6 +697,48 @@ extern "C" vbw_status vbw_stream_restore(vbw_stream_t s, const void* host_buf, s
 // ------------------------------------------------------------------------------------------------
 // batches
 
+static void batch_free(vbw_batch_s* bt)
+{
+    if (bt->s_h2d) {
+        cudaStreamSynchronize(bt->s_d2h);
+        cudaStreamDestroy(bt->s_h2d);
+        cudaStreamDestroy(bt->s_comp);
+        cudaStreamDestroy(bt->s_d2h);
+        cudaEventDestroy(bt->ev_start);
+        cudaEventDestroy(bt->ev_h);
+        cudaEventDestroy(bt->ev_c);
+        cudaEventDestroy(bt->ev_done);
+    }
+    if (bt->s_side) {
+        cudaStreamSynchronize(bt->s_side);
+        cudaStreamDestroy(bt->s_side);
+        cudaEventDestroy(bt->ev_fork);
+        cudaEventDestroy(bt->ev_join);
+    }
+    for (auto& G : bt->groups) {
+        cudaFree(G.d_jobs);
+        cudaFree(G.d_tiles);
+    }
+    cudaFree(bt->d_mjobs);
+    cudaFree(bt->d_mtiles);
+    cudaFree(bt->d_bands);
+    delete bt;
+}
+
+template <class T>
+static cudaError_t upload(T** dst, const std::vector<T>& v)
+{
+    *dst = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Plans a mixed launch can take: overlap N/4 and N <= 1024 (N = 2048 keeps its own kernel, whose
+// register and shared-memory footprint would otherwise apply to every N).
+static bool mixable(const vbw_plan_s* p) { return p->O == p->N / 4 && p->N <= 1024; }
+
 extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t* out)
 {
     if (!out) return fail(VBW_ERR_INVALID_ARG, "out is NULL");
@@ -634,6 +755,7 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
         if (g.nsamples > 0 && ranges_overlap(g.in, g.out, sizeof(float2) * (size_t)g.nsamples))
             return fail(VBW_ERR_INVALID_ARG, "signal %d: in and out overlap", i);
         const int64_t nb = (g.nsamples + g.plan->M - 1) / g.plan->M;
+        if (nb > INT32_MAX) return fail(VBW_ERR_INVALID_ARG, "signal %d: too many blocks", i);
         if (g.band_per_block) {
             for (int64_t b = 0; b < nb; ++b)
                 if (check_band(g.plan, g.band_per_block[b]) != VBW_OK)
@@ -646,10 +768,14 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
     }
     vbw_batch_s* bt = new (std::nothrow) vbw_batch_s();
     if (!bt) return fail(VBW_ERR_NOMEM, "host allocation failed");
+    memset(&bt->margs, 0, sizeof(bt->margs));
+    bt->sigs.assign(sig, sig + n);
+
+    // per-block bands of every signal, one device array
     std::vector<int32_t> bands;
     bands.reserve((size_t)total_blocks);
-    std::map<vbw_plan_s*, std::vector<int>> by_plan;
     std::vector<int64_t> band_off(n, 0);
+    std::map<vbw_plan_s*, std::vector<int>> by_plan;
     for (int i = 0; i < n; ++i) {
         const vbw_signal& g = sig[i];
         const int64_t nb = (g.nsamples + g.plan->M - 1) / g.plan->M;
@@ -657,83 +783,112 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
         for (int64_t b = 0; b < nb; ++b) bands.push_back(g.band_per_block ? g.band_per_block[b] : g.band);
         if (nb > 0) by_plan[g.plan].push_back(i);
     }
-    auto cleanup = [&]() {
-        for (auto& gr : bt->groups) {
-            cudaFree(gr.d_jobs);
-            cudaFree(gr.d_tiles);
-        }
-        cudaFree(bt->d_bands);
-        delete bt;
-    };
-    if (!bands.empty()) {
-        if (cudaMalloc(&bt->d_bands, sizeof(int32_t) * bands.size()) != cudaSuccess) {
-            cudaGetLastError();
-            cleanup();
-            return fail(VBW_ERR_NOMEM, "batch band array allocation failed");
-        }
-        cudaError_t e = cudaMemcpy(bt->d_bands, bands.data(), sizeof(int32_t) * bands.size(),
-                                   cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cleanup();
-            return fail(VBW_ERR_CUDA, "batch band upload failed: %s", cudaGetErrorString(e));
-        }
+    cudaError_t e = upload(&bt->d_bands, bands);
+    if (e != cudaSuccess) {
+        batch_free(bt);
+        return fail(VBW_ERR_NOMEM, "batch band upload failed: %s", cudaGetErrorString(e));
     }
+
+    // one group per plan (single-plan launches), and the mixed work list over mixable plans
+    std::vector<OlsJob> mjobs;
+    std::vector<int2> mtiles;
+    int nmixed = 0;
+    size_t mixed_warp_bytes = 0;
+    int32_t tw_off = 0;
     for (auto& kv : by_plan) {
         vbw_plan_s* p = kv.first;
         const int B = blocks_per_warp(p->N);
+        const bool mix = mixable(p) && nmixed < kMaxMixedPlans;
+        const int plan_idx = mix ? nmixed : 0;
         std::vector<OlsJob> jobs;
         std::vector<int2> tiles;
-        std::vector<int> gr_sig;
-        std::vector<int64_t> gr_off;
+        BatchGroup gr;
+        gr.plan = p;
         for (int i : kv.second) {
             const vbw_signal& g = sig[i];
             OlsJob j;
             memset(&j, 0, sizeof(j));
             j.in = (const float2*)g.in;
             j.out = (float2*)g.out;
-            j.tail_in = nullptr;
-            j.tail_out = nullptr;
             j.band = bt->d_bands + band_off[i];
             j.nsamp = g.nsamples;
             j.band0 = bands[(size_t)band_off[i]];
+            j.plan = 0;
             const int64_t nb = (g.nsamples + p->M - 1) / p->M;
-            if (nb > INT32_MAX) {
-                cleanup();
-                return fail(VBW_ERR_INVALID_ARG, "signal %d: too many blocks", i);
-            }
-            const int ji = (int)jobs.size();
+            gr.sig.push_back(i);
+            gr.tile_off.push_back((int64_t)tiles.size());
+            for (int64_t b = 0; b < nb; b += B) tiles.push_back(make_int2((int)jobs.size(), (int)b));
             jobs.push_back(j);
-            gr_sig.push_back(i);
-            gr_off.push_back((int64_t)tiles.size());
-            for (int64_t b = 0; b < nb; b += B) tiles.push_back(make_int2(ji, (int)b));
+            gr.cost += (double)nb * p->N * std::log2((double)p->N);
+            if (mix) {
+                j.plan = plan_idx;
+                for (int64_t b = 0; b < nb; b += B) mtiles.push_back(make_int2((int)mjobs.size(), (int)b));
+                mjobs.push_back(j);
+            }
         }
-        gr_off.push_back((int64_t)tiles.size());
-        BatchGroup gr;
-        gr.plan = p;
+        gr.tile_off.push_back((int64_t)tiles.size());
         gr.ntiles = (int64_t)tiles.size();
-        gr.sig.swap(gr_sig);
-        gr.tile_off.swap(gr_off);
+        cudaError_t e1 = upload(&gr.d_jobs, jobs);
+        cudaError_t e2 = e1 == cudaSuccess ? upload(&gr.d_tiles, tiles) : e1;
         bt->groups.push_back(gr);
-        BatchGroup& G = bt->groups.back();
-        if (cudaMalloc(&G.d_jobs, sizeof(OlsJob) * jobs.size()) != cudaSuccess ||
-            cudaMalloc(&G.d_tiles, sizeof(int2) * tiles.size()) != cudaSuccess) {
-            cudaGetLastError();
-            cleanup();
-            return fail(VBW_ERR_NOMEM, "batch work-list allocation failed");
+        if (e2 != cudaSuccess) {
+            batch_free(bt);
+            return fail(VBW_ERR_NOMEM, "batch work-list upload failed: %s", cudaGetErrorString(e2));
         }
-        cudaError_t e1 = cudaMemcpy(G.d_jobs, jobs.data(), sizeof(OlsJob) * jobs.size(), cudaMemcpyHostToDevice);
-        cudaError_t e2 = cudaMemcpy(G.d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            cleanup();
-            return fail(VBW_ERR_CUDA, "batch work-list upload failed");
+        if (mix) {
+            MixedPlan& mp = bt->margs.plans[nmixed];
+            mp.tw = p->d_tw;
+            mp.V = p->d_V;
+            mp.N = p->N;
+            mp.LV = p->LV;
+            mp.tw_off = tw_off;
+            mp.tw_len = twiddle_entries(p->N);
+            tw_off += (mp.tw_len + 1) / 2 * 2;   // keep every table 16-byte aligned
+            mixed_warp_bytes = std::max(mixed_warp_bytes, ols_warp_bytes(p->N));
+            bt->mixed_groups.push_back((int)bt->groups.size() - 1);
+            bt->mixed_cost += gr.cost;
+            ++nmixed;
         }
     }
-    bt->sigs.assign(sig, sig + n);
+    if (nmixed > 0) {
+        cudaError_t e1 = upload(&bt->d_mjobs, mjobs);
+        cudaError_t e2 = e1 == cudaSuccess ? upload(&bt->d_mtiles, mtiles) : e1;
+        if (e2 != cudaSuccess) {
+            batch_free(bt);
+            return fail(VBW_ERR_NOMEM, "mixed work-list upload failed: %s", cudaGetErrorString(e2));
+        }
+        bt->margs.jobs = bt->d_mjobs;
+        bt->margs.tiles = bt->d_mtiles;
+        bt->margs.ntiles = (int64_t)mtiles.size();
+        bt->margs.nplans = nmixed;
+        bt->margs.tw_bytes = (int32_t)(sizeof(float2) * (size_t)tw_off);
+        bt->margs.warp_bytes = (int32_t)mixed_warp_bytes;
+        bt->margs.status = bt->groups[bt->mixed_groups[0]].plan->d_status;
+    }
+    if (cudaStreamCreateWithFlags(&bt->s_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        batch_free(bt);
+        return fail(VBW_ERR_CUDA, "batch stream creation failed");
+    }
     *out = bt;
     return ok();
 }
 
-static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t1, cudaStream_t st)
+extern "C" vbw_status vbw_batch_set_mode(vbw_batch_t bt, int mode, double mixed_share)
+{
+    if (!bt) return fail(VBW_ERR_INVALID_ARG, "batch is NULL");
+    if (mode < VBW_BATCH_AUTO || mode > VBW_BATCH_MIXED)
+        return fail(VBW_ERR_INVALID_ARG, "unknown batch mode %d", mode);
+    if (!(mixed_share >= 0.0 && mixed_share < 1.0))
+        return fail(VBW_ERR_INVALID_ARG, "mixed_share must be in [0, 1)");
+    bt->mode = mode;
+    bt->split = mixed_share;
+    return ok();
+}
+
+static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t1, cudaStream_t st,
+                                      int max_ctas = 0)
 {
     vbw_plan_s* p = G.plan;
     OlsArgs a;
@@ -741,11 +896,72 @@ static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t
     a.jobs = G.d_jobs;
     a.tiles = G.d_tiles + t0;
     a.ntiles = t1 - t0;
-    a.tw = p->d_tw;
-    a.V = p->d_V;
-    a.overlap = p->O;
-    a.LV = p->LV;
-    return launch_fp32(p->N, a, p->warps, p->sms, st);
+    fill_plan_args(a, p);
+    return launch_fp32(p->N, a, p->sms, st, max_ctas);
+}
+
+// Device-side run of a prepared batch. PER_PLAN: one full-GPU persistent launch per plan, in
+// order. MIXED: one persistent launch over every mixable plan, with the remaining plans (N = 2048
+// or other overlaps) launched beside it on a forked stream; the SMs are shared in proportion to
+// the transform work unless a share was set. AUTO: MIXED when at least two plans mix.
+static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st)
+{
+    int launches = 0;
+    const bool use_mixed = bt->mode == VBW_BATCH_MIXED
+                               ? !bt->mixed_groups.empty()
+                               : (bt->mode == VBW_BATCH_AUTO && bt->mixed_groups.size() >= 2);
+    if (!use_mixed) {
+        for (auto& G : bt->groups) {
+            cudaError_t e = launch_group_range(G, 0, G.ntiles, st);
+            if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+            ++launches;
+        }
+        bt->last_launches = launches;
+        return VBW_OK;
+    }
+    double rest_cost = 0;
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi)
+        if (std::find(bt->mixed_groups.begin(), bt->mixed_groups.end(), (int)gi) == bt->mixed_groups.end())
+            rest_cost += bt->groups[gi].cost;
+    const int sms = bt->groups[0].plan->sms;
+    double share = bt->split > 0 ? bt->split : bt->mixed_cost / (bt->mixed_cost + rest_cost);
+    if (rest_cost == 0) share = 1.0;
+    int mixed_sms = std::max(1, std::min(sms, (int)std::lround(share * sms)));
+    if (rest_cost > 0 && mixed_sms == sms) mixed_sms = sms - 1;
+    const int mwarps = 4;
+    int mixed_per_sm = 0;
+    {
+        // CTAs of the mixed kernel that fit on one SM decide how many CTAs its SM share is
+        const size_t smem = (size_t)bt->margs.tw_bytes + (size_t)mwarps * bt->margs.warp_bytes;
+        mixed_per_sm = (int)std::max<size_t>(1, (228 * 1024) / std::max<size_t>(smem, 1));
+    }
+    if (rest_cost > 0) {
+        VBW_CUDA(cudaEventRecord(bt->ev_fork, st));
+        VBW_CUDA(cudaStreamWaitEvent(bt->s_side, bt->ev_fork, 0));
+    }
+    MixedArgs ma = bt->margs;
+    ma.wait_limit = g_wait_limit_debug ? 2000000LL : 0;
+    ma.debug = g_wait_limit_debug ? 1 : 0;
+    int grid = 0;
+    cudaError_t e = launch_ols_mixed(ma, 1024, mwarps, sms, mixed_per_sm * mixed_sms, st, &grid);
+    if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "mixed launch failed: %s", cudaGetErrorString(e));
+    ++launches;
+    if (rest_cost > 0) {
+        const int side_sms = sms - mixed_sms;
+        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+            if (std::find(bt->mixed_groups.begin(), bt->mixed_groups.end(), (int)gi) != bt->mixed_groups.end())
+                continue;
+            const BatchGroup& G = bt->groups[gi];
+            const int per_sm = G.plan->N >= 2048 ? 2 : 4;
+            e = launch_group_range(G, 0, G.ntiles, bt->s_side, per_sm * side_sms);
+            if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
+            ++launches;
+        }
+        VBW_CUDA(cudaEventRecord(bt->ev_join, bt->s_side));
+        VBW_CUDA(cudaStreamWaitEvent(st, bt->ev_join, 0));
+    }
+    bt->last_launches = launches;
+    return VBW_OK;
 }
 
 extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host_in,
@@ -812,15 +1028,8 @@ extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host
 extern "C" vbw_status vbw_batch_run(vbw_batch_t bt, void* cuda_stream)
 {
     if (!bt) return fail(VBW_ERR_INVALID_ARG, "batch is NULL");
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    int launches = 0;
-    for (auto& G : bt->groups) {
-        cudaError_t e = launch_group_range(G, 0, G.ntiles, st);
-        if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
-        ++launches;
-    }
-    bt->last_launches = launches;
-    return ok();
+    vbw_status st = batch_launch(bt, (cudaStream_t)cuda_stream);
+    return st == VBW_OK ? ok() : st;
 }
 
 extern "C" vbw_status vbw_batch_launches(vbw_batch_t bt, int* launches)
@@ -833,22 +1042,7 @@ extern "C" vbw_status vbw_batch_launches(vbw_batch_t bt, int* launches)
 extern "C" vbw_status vbw_batch_destroy(vbw_batch_t bt)
 {
     if (!bt) return fail(VBW_ERR_INVALID_ARG, "batch is NULL");
-    if (bt->s_h2d) {
-        cudaStreamSynchronize(bt->s_d2h);
-        cudaStreamDestroy(bt->s_h2d);
-        cudaStreamDestroy(bt->s_comp);
-        cudaStreamDestroy(bt->s_d2h);
-        cudaEventDestroy(bt->ev_start);
-        cudaEventDestroy(bt->ev_h);
-        cudaEventDestroy(bt->ev_c);
-        cudaEventDestroy(bt->ev_done);
-    }
-    for (auto& G : bt->groups) {
-        cudaFree(G.d_jobs);
-        cudaFree(G.d_tiles);
-    }
-    cudaFree(bt->d_bands);
-    delete bt;
+    batch_free(bt);
     return ok();
 }
 

@@ -107,7 +107,7 @@ struct OlsJob {
     const int32_t* band;   // device, k1 per block; nullptr = band0 (plus inline changes)
     int64_t nsamp;
     int32_t band0;
-    int32_t pad_;
+    int32_t plan;          // index into MixedArgs::plans (mixed launches; 0 otherwise)
 };
 
 constexpr int kInlineChanges = 16;
@@ -125,6 +125,33 @@ struct OlsArgs {
     int32_t overlap;
     int32_t LV;
     int* status;          // device status word (bit flags, e.g. a bounded wait that gave up) or nullptr
+    int64_t wait_limit;   // bound of device-side waits in SM cycles (0 = default, about 2 s)
+    int32_t debug;        // test hook, bit 0: skip the staging copies (their waits then run out)
+    int32_t pad_;
+};
+
+// One plan of a mixed-plan launch (overlap N/4).
+struct MixedPlan {
+    const float2* tw;     // device twiddle rows of this plan
+    const float* V;       // device transition samples
+    int32_t N, LV;
+    int32_t tw_off;       // offset of the rows in shared memory (float2 units, 16-byte aligned)
+    int32_t tw_len;       // number of float2 entries
+};
+
+constexpr int kMaxMixedPlans = 8;
+
+struct MixedArgs {
+    const OlsJob* jobs;   // jobs grouped by plan
+    const int2* tiles;    // per warp-tile (job index, first block)
+    int64_t ntiles;
+    MixedPlan plans[kMaxMixedPlans];
+    int32_t nplans;
+    int32_t tw_bytes;     // shared bytes of all twiddle rows
+    int32_t warp_bytes;   // per-warp region (largest N of the launch)
+    int32_t debug;        // as OlsArgs::debug
+    int* status;
+    int64_t wait_limit;   // as OlsArgs::wait_limit
 };
 
 }  // namespace vbw

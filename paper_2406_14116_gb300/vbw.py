@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "VBW_OK", 1: "VBW_ERR_INVALID_ARG", 2: "VBW_ERR_BAND_RANGE", 
                 4: "VBW_ERR_CUDA", 5: "VBW_ERR_TIMEOUT", 6: "VBW_ERR_BUSY", 7: "VBW_ERR_STATE",
                 8: "VBW_ERR_UNSUPPORTED"}
 VBW_PREC_FP32 = 0
+VBW_BATCH_AUTO, VBW_BATCH_PER_PLAN, VBW_BATCH_MIXED = 0, 1, 2
 
 
 class VbwError(RuntimeError):
@@ -79,6 +80,10 @@ def lib():
         "vbw_batch_destroy": [p],
         "vbw_batch_launches": [p, p],
         "vbw_debug_export_HR": [p, i32, p],
+        "vbw_batch_set_mode": [p, i32, ctypes.c_double],
+        "vbw_tune_set": [i32, i32],
+        "vbw_plan_status": [p, p, i32],
+        "vbw_debug_set": [i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -247,6 +252,32 @@ def vbw_batch_launches(b: int) -> int:
     return v.value
 
 
+def vbw_batch_set_mode(b: int, mode: int, mixed_share: float = 0.0):
+    _check(lib().vbw_batch_set_mode(b, mode, mixed_share))
+
+
+def vbw_tune_set(N: int, warps: int):
+    _check(lib().vbw_tune_set(N, warps))
+
+
+def vbw_plan_status(plan: int, clear: bool = False) -> int:
+    """Returns the plan's device status word; raises VbwError(VBW_ERR_TIMEOUT) if bit 0 is set."""
+    v = ctypes.c_int(0)
+    _check(lib().vbw_plan_status(plan, ctypes.byref(v), 1 if clear else 0))
+    return v.value
+
+
+def vbw_plan_status_raw(plan: int, clear: bool = False) -> tuple[int, int]:
+    """(status code, flags) without raising."""
+    v = ctypes.c_int(0)
+    rc = lib().vbw_plan_status(plan, ctypes.byref(v), 1 if clear else 0)
+    return rc, v.value
+
+
+def vbw_debug_set(flags: int):
+    _check(lib().vbw_debug_set(flags))
+
+
 def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
     N = vbw_plan_info(plan)[0]
     out = np.empty(N, dtype=np.float32)
@@ -342,6 +373,9 @@ class Batch:
 
     def run_host(self, host_in, host_out, cuda_stream=None):
         vbw_batch_run_host(self.handle, host_in, host_out, cuda_stream)
+
+    def set_mode(self, mode: int, mixed_share: float = 0.0):
+        vbw_batch_set_mode(self.handle, mode, mixed_share)
 
     @property
     def launches(self) -> int:

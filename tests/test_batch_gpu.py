@@ -1,0 +1,162 @@
+"""Batched filtering of many streams with mixed lengths, transform sizes and bands (one prepared
+batch, single-plan or mixed-plan persistent launches, CUDA-graph replay), the bounded-wait failure
+path, all through the C ABI and checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import assert_parity
+from paper_2406_14116_gb300 import vbw
+from paper_2406_14116_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_batch(torch, nstreams=40, seed=33, log2_lo=10.0, log2_hi=15.0):
+    w = wl.mixed(seed=seed, nstreams=nstreams, log2_lo=log2_lo, log2_hi=log2_hi)
+    plans = {N: vbw.Plan(N, N // 4, w.V) for N in (128, 256, 512, 1024, 2048)}
+    xs = [torch.from_numpy(s.x).cuda() for s in w.signals]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    rows = [(plans[s.N], x, y, s.band) for s, x, y in zip(w.signals, xs, ys)]
+    return w, plans, xs, ys, vbw.Batch(rows)
+
+
+def test_mixed_batch_all_modes_match_oracle_and_each_other(cuda):
+    torch = cuda
+    w, plans, xs, ys, b = mixed_batch(torch)
+    outs = {}
+    for mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO):
+        for y in ys:
+            y.fill_(float("nan"))
+        b.set_mode(mode)
+        b.run()
+        torch.cuda.synchronize()
+        outs[mode] = [y.cpu().numpy() for y in ys]
+        if mode == vbw.VBW_BATCH_MIXED:
+            assert b.launches == 2      # one mixed launch + the N = 2048 plan beside it
+        if mode == vbw.VBW_BATCH_PER_PLAN:
+            assert b.launches == 5
+    for s, y in zip(w.signals, outs[vbw.VBW_BATCH_PER_PLAN]):
+        ref = oracle.filter(s.N, s.overlap, w.V, s.band, s.x)
+        assert_parity(y, ref, what=f"stream {s.stream} N={s.N} len={len(s.x)}")
+    for mode in (vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO):
+        for a, c in zip(outs[vbw.VBW_BATCH_PER_PLAN], outs[mode]):
+            np.testing.assert_array_equal(a, c)
+
+
+def test_mixed_share_and_single_stream_batch(cuda):
+    torch = cuda
+    w, plans, xs, ys, b = mixed_batch(torch, nstreams=12, seed=7)
+    b.set_mode(vbw.VBW_BATCH_MIXED, 0.5)
+    b.run()
+    torch.cuda.synchronize()
+    for s, y in zip(w.signals, ys):
+        assert_parity(y.cpu().numpy(), oracle.filter(s.N, s.overlap, w.V, s.band, s.x))
+    with pytest.raises(vbw.VbwError):
+        b.set_mode(7)
+    with pytest.raises(vbw.VbwError):
+        b.set_mode(vbw.VBW_BATCH_MIXED, 1.5)
+
+
+def test_batch_replays_in_cuda_graph(cuda):
+    torch = cuda
+    w, plans, xs, ys, b = mixed_batch(torch, nstreams=24, seed=5)
+    b.set_mode(vbw.VBW_BATCH_MIXED)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(s)                     # warm-up (lazy attribute setting happens outside capture)
+    torch.cuda.synchronize()
+    ref = [y.clone() for y in ys]
+    for y in ys:
+        y.fill_(float("nan"))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(s)
+    for _ in range(3):
+        for y in ys:
+            y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for a, c in zip(ref, ys):
+            assert torch.equal(a, c)
+
+
+def test_empty_and_tiny_signals_in_batch(cuda):
+    torch = cuda
+    V = wl.transition_table(3, 12)
+    p1 = vbw.Plan(256, 64, V)
+    p2 = vbw.Plan(1024, 256, V)
+    sig = [np.zeros(0, np.complex64), wl.complex_gaussian(3, 1, 5), wl.complex_gaussian(3, 2, 192),
+           wl.complex_gaussian(3, 3, 193), wl.complex_gaussian(3, 4, 3000)]
+    plans = [p1, p1, p1, p2, p2]
+    xs = [torch.from_numpy(x).cuda() if len(x) else torch.zeros(0, dtype=torch.complex64, device="cuda")
+          for x in sig]
+    ys = [torch.zeros_like(x) for x in xs]
+    b = vbw.Batch([(p, x, y, 9) for p, x, y in zip(plans, xs, ys)])
+    b.run()
+    torch.cuda.synchronize()
+    for p, x, y in zip(plans, sig, ys):
+        if len(x):
+            assert_parity(y.cpu().numpy(), oracle.filter(p.N, p.overlap, V, 9, x))
+
+
+def test_bounded_wait_runs_out_and_reports(cuda):
+    """A staged copy that never arrives (test hook: the copy is not issued) makes the bounded
+    mbarrier wait run out: the kernel sets the status word and the warp returns; the context stays
+    usable and the next launch is correct."""
+    torch = cuda
+    N, O = 1024, 256
+    M = N - O
+    nb = 8000                     # more blocks than resident warps, so warps stage a next block
+    V = wl.transition_table(4, 12)
+    plan = vbw.Plan(N, O, V)
+    x = wl.complex_gaussian(4, 0, nb * M)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    assert vbw.vbw_plan_status(plan.handle, clear=True) == 0
+    vbw.vbw_debug_set(1)
+    try:
+        s = vbw.Stream(plan, 100)
+        s.filter(xd, yd, nb)
+        torch.cuda.synchronize()
+    finally:
+        vbw.vbw_debug_set(0)
+    rc, flags = vbw.vbw_plan_status_raw(plan.handle, clear=True)
+    assert rc == 5 and flags & 1
+    assert vbw.vbw_plan_status(plan.handle) == 0
+    s = vbw.Stream(plan, 100)
+    s.filter(xd, yd, nb)
+    torch.cuda.synchronize()
+    assert vbw.vbw_plan_status(plan.handle) == 0
+    y = yd.cpu().numpy()
+    for b0, cnt in ((0, 64), (nb // 2, 32), (nb - 64, 64)):
+        ref = oracle.filter(N, O, V, 100, x, blocks=(b0, cnt))
+        sl = slice(b0 * M, (b0 + cnt) * M)
+        assert_parity(y[sl], ref[sl], what=f"blocks {b0}..{b0 + cnt}")
+
+
+def test_tune_set_changes_shape_not_result(cuda):
+    torch = cuda
+    N, O = 512, 128
+    M = N - O
+    V = wl.transition_table(9, 12)
+    plan = vbw.Plan(N, O, V)
+    x = wl.complex_gaussian(9, 0, 300 * M)
+    xd = torch.from_numpy(x).cuda()
+    outs = []
+    try:
+        for w in (4, 8, 0):
+            vbw.vbw_tune_set(N, w)
+            yd = torch.zeros_like(xd)
+            vbw.Stream(plan, 77).filter(xd, yd, 300)
+            torch.cuda.synchronize()
+            outs.append(yd.cpu().numpy())
+    finally:
+        vbw.vbw_tune_set(N, 0)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    with pytest.raises(vbw.VbwError):
+        vbw.vbw_tune_set(300, 4)
+    with pytest.raises(vbw.VbwError):
+        vbw.vbw_tune_set(512, 6)
