@@ -159,10 +159,11 @@ vbw_status vbw_batch_launches(vbw_batch_t batch, int* launches);
 enum { VBW_BATCH_AUTO = 0, VBW_BATCH_PER_PLAN = 1, VBW_BATCH_MIXED = 2 };
 vbw_status vbw_batch_set_mode(vbw_batch_t batch, int mode, double mixed_share);
 
-/* Tuning: warps per CTA (4 or 8; 0 restores the default) of the single-plan kernel for transform
- * size N, for every later launch in this process. The autotuner (paper_2406_14116_gb300/tune.py)
- * measures the choices and writes them to a cache that it loads through this call. */
-vbw_status vbw_tune_set(int N, int warps);
+/* Tuning of the single-plan kernel for transform size N, for every later launch in this process:
+ * warps per CTA (4 or 8; 0 = default) and a cap on resident CTAs per SM (0 = as many as fit).
+ * The autotuner (paper_2406_14116_gb300/tune.py) measures the choices on the current GPU, keeps
+ * them in a JSON cache and applies them through this call. Errors: VBW_ERR_INVALID_ARG. */
+vbw_status vbw_tune_set(int N, int warps, int ctas_per_sm);
 
 /* Device status word of a plan's launches (synchronizes the device): bit 0 = a bounded device-side
  * wait gave up (the kernel's warp stopped and its outputs are incomplete). Returns VBW_ERR_TIMEOUT

@@ -152,6 +152,7 @@ struct vbw_batch_s {
 
 static std::mutex g_tune_mu;
 static int g_tune_warps[5] = {0, 0, 0, 0, 0};   // N = 128 << i; 0 = default
+static int g_tune_ctas[5] = {0, 0, 0, 0, 0};    // resident CTAs per SM cap; 0 = occupancy limit
 static int g_wait_limit_debug = 0;               // test hook: skip staging copies, short waits
 
 static int n_index(int N)
@@ -208,10 +209,19 @@ static int warps_for(int N)
     return (N <= 1024) ? 8 : 4;
 }
 
+static int ctas_cap_for(int N, int sms)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int i = n_index(N);
+    return (i >= 0 && g_tune_ctas[i] > 0) ? g_tune_ctas[i] * sms : 0;
+}
+
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st, int max_ctas = 0)
 {
     int grid = 0;
     const int warps = warps_for(N);
+    const int cap = ctas_cap_for(N, sms);
+    if (cap > 0 && (max_ctas == 0 || cap < max_ctas)) max_ctas = cap;
     switch (N) {
     case 128: return launch_ols_fp32<128>(a, warps, sms, max_ctas, st, &grid);
     case 256: return launch_ols_fp32<256>(a, warps, sms, max_ctas, st, &grid);
@@ -329,14 +339,17 @@ extern "C" vbw_status vbw_plan_status(vbw_plan_t p, int* flags, int clear)
     return ok();
 }
 
-extern "C" vbw_status vbw_tune_set(int N, int warps)
+extern "C" vbw_status vbw_tune_set(int N, int warps, int ctas_per_sm)
 {
     const int i = n_index(N);
     if (i < 0) return fail(VBW_ERR_INVALID_ARG, "N=%d is not a supported transform size", N);
     if (warps != 0 && warps != 4 && warps != 8)
         return fail(VBW_ERR_INVALID_ARG, "warps=%d: must be 0 (default), 4 or 8", warps);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32)
+        return fail(VBW_ERR_INVALID_ARG, "ctas_per_sm=%d: must be in [0, 32]", ctas_per_sm);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_warps[i] = warps;
+    g_tune_ctas[i] = ctas_per_sm;
     return ok();
 }
 

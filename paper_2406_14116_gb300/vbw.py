@@ -81,7 +81,7 @@ def lib():
         "vbw_batch_launches": [p, p],
         "vbw_debug_export_HR": [p, i32, p],
         "vbw_batch_set_mode": [p, i32, ctypes.c_double],
-        "vbw_tune_set": [i32, i32],
+        "vbw_tune_set": [i32, i32, i32],
         "vbw_plan_status": [p, p, i32],
         "vbw_debug_set": [i32],
     }
@@ -256,8 +256,8 @@ def vbw_batch_set_mode(b: int, mode: int, mixed_share: float = 0.0):
     _check(lib().vbw_batch_set_mode(b, mode, mixed_share))
 
 
-def vbw_tune_set(N: int, warps: int):
-    _check(lib().vbw_tune_set(N, warps))
+def vbw_tune_set(N: int, warps: int, ctas_per_sm: int = 0):
+    _check(lib().vbw_tune_set(N, warps, ctas_per_sm))
 
 
 def vbw_plan_status(plan: int, clear: bool = False) -> int:
