@@ -409,7 +409,9 @@ def native_arm(args):
             plans[key] = vbw.Plan(s.N, s.overlap, V)
     batch = vbw.Batch([(plans[(s.N, s.overlap)], d_in[offs[i]:offs[i + 1]],
                         d_out[offs[i]:offs[i + 1]], s.band) for i, s in enumerate(streams)])
-    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()          # graphs cannot be captured on the default stream
+    torch.cuda.set_stream(side)
+    stream = side
     if len(plans) > 1 and not args.no_tune:
         cfg["batch_mode"] = {k: v for k, v in tune.tune_mixed(torch, batch).items() if k != "table"}
 
@@ -501,7 +503,9 @@ def native_arm(args):
         dt = float(tt.item())
         e2e = {"value": total * world * k_e2e / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
-               "steps": k_e2e, "api": "vbw_batch_run_host (pinned host buffers)"}
+               "steps": k_e2e,
+               "api": "vbw_batch_run_host, pinned host buffers (zero copy: the kernels read and "
+                      "write host memory over NVLink-C2C)"}
         step()
         torch.cuda.synchronize()
         n_chk = min(total, 1 << 20)

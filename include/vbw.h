@@ -137,10 +137,14 @@ vbw_status vbw_batch_create(const vbw_signal* signals, int nsignals, vbw_batch_t
 vbw_status vbw_batch_run(vbw_batch_t batch, void* cuda_stream);
 
 /* Runs a prepared batch from HOST buffers: host_in[i] and host_out[i] hold signal i's nsamples
- * samples (pinned memory gives overlapped copies; pageable memory works but serializes them).
- * The batch's device in/out arrays serve as staging. Copies in, kernels and copies out are
- * pipelined over groups of signals on library-owned streams that start after the work already
- * queued on cuda_stream; the call returns when every host_out is written. */
+ * samples; the call returns when every host_out is written, ordered after the work already queued
+ * on cuda_stream.
+ *   - All buffers pinned (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory): zero copy. The
+ *     kernels read and write host memory directly over the coherent CPU-GPU link (Grace-Blackwell
+ *     NVLink-C2C), with plain loads and stores; nothing is staged. VBW_ZERO_COPY=0 disables it.
+ *   - Otherwise: staged. The batch's device in/out arrays hold the data; copies in (merged where
+ *     signals are contiguous on both sides), kernels and copies out are pipelined over groups of
+ *     signals on library-owned streams (pageable memory works but serializes the copies). */
 vbw_status vbw_batch_run_host(vbw_batch_t batch, const void* const* host_in, void* const* host_out,
                               void* cuda_stream);
 vbw_status vbw_batch_destroy(vbw_batch_t batch);

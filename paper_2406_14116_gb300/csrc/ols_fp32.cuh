@@ -275,6 +275,7 @@ struct TileCtl {
     int* status;          // device status word
     long long wait_limit; // bounded-wait limit in SM cycles
     int debug;            // bit 0: mark blocks staged without issuing the copies (test hook)
+    bool bulk;            // TMA staging and bulk L2 prefetch allowed (signals in device memory)
 };
 
 template <int N, bool QOVL, class Src>
@@ -304,13 +305,17 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
         const int k1 = src.band(job, blk, active);
         const int key = active ? ((plan << 16) | k1) : ws.table_key;
 
-        // ---- ask L2 for the samples the warp's next tile adds (the rest is this span)
-        if (lane == 0 && has_next) {
-            const int64_t e = (blk + B - 1) * (int64_t)M - O + N;
+        // ---- ask L2 for the samples the warp's next tile adds (the rest is this span). The bulk
+        //      prefetch needs a 16-byte aligned start and a multiple of 16 bytes: a stream whose
+        //      base is only 8-byte aligned starts one sample later.
+        if (lane == 0 && has_next && ctl.bulk) {
+            int64_t e = (blk + B - 1) * (int64_t)M - O + N;
             int64_t e2 = e + (int64_t)B * M;
             if (e2 > nsamp) e2 = nsamp;
+            if (e >= 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) != 0) ++e;
             const int64_t cnt = (e2 - e) & ~int64_t(1);
-            if (e >= 0 && cnt > 0) prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+            if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) == 0)
+                prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
         }
 
         // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
@@ -371,7 +376,7 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     for (int pass = 0; pass < 2; ++pass) {
         four_step_dft<N>(x, buf, twrow, t, [&]() {
 #if VBW_TMA_STAGE
-            if (pass != 1 || !has_next) return;
+            if (pass != 1 || !has_next || !ctl.bulk) return;
             // the lane group's next block (same plan only): TMA-staged when its span is interior
             OlsJob nj;
             int64_t nb;
@@ -472,7 +477,8 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
     __syncthreads();
 
     WarpState ws{-1, false, 0u};
-    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug};
+    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
+                      (a.flags & kOlsNoBulk) == 0};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
@@ -506,7 +512,8 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
     __syncthreads();
 
     const JobListSource src{a.jobs, a.tiles};
-    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug};
+    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
+                      (a.flags & kOlsNoBulk) == 0};
     WarpState ws{-1, false, 0u};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);

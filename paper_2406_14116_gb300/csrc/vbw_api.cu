@@ -143,6 +143,10 @@ struct vbw_batch_s {
     double split = 0;               // share of the SMs for the mixed launch (0 = by cost)
     cudaStream_t s_side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // zero-copy runs from pinned host memory: job arrays with host addresses (per group, mixed)
+    std::vector<OlsJob*> d_zjobs;
+    OlsJob* d_zmjobs = nullptr;
+    std::vector<const void*> z_in, z_out;   // host pointers the zero-copy arrays hold
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_start = nullptr, ev_h = nullptr, ev_c = nullptr, ev_done = nullptr;
 };
@@ -180,6 +184,9 @@ static vbw_status check_band(const vbw_plan_s* p, int band)
                     p->N, p->LV);
     return VBW_OK;
 }
+
+// complex64 samples need 8-byte alignment
+static bool misaligned(const void* p) { return ((uintptr_t)p & 7) != 0; }
 
 static bool ranges_overlap(const void* a, const void* b, size_t bytes)
 {
@@ -543,6 +550,7 @@ extern "C" vbw_status vbw_filter(vbw_stream_t s, const void* in, void* out, int6
     if (nblocks < 0) return fail(VBW_ERR_INVALID_ARG, "nblocks < 0");
     if (nblocks == 0) return ok();
     if (!in || !out) return fail(VBW_ERR_INVALID_ARG, "in/out is NULL");
+    if (misaligned(in) || misaligned(out)) return fail(VBW_ERR_INVALID_ARG, "in/out not 8-byte aligned");
     const size_t bytes = sizeof(float2) * (size_t)nblocks * s->plan->M;
     if (ranges_overlap(in, out, bytes)) return fail(VBW_ERR_INVALID_ARG, "in and out overlap");
     vbw_status st = filter_blocks(s, (const float2*)in, (float2*)out, nblocks);
@@ -557,6 +565,8 @@ extern "C" vbw_status vbw_flush(vbw_stream_t s, const void* in, void* out, int n
         return fail(VBW_ERR_INVALID_ARG, "nvalid=%d outside [0, M)", nvalid);
     if (nvalid > 0) {
         if (!in || !out) return fail(VBW_ERR_INVALID_ARG, "in/out is NULL");
+        if (misaligned(in) || misaligned(out))
+            return fail(VBW_ERR_INVALID_ARG, "in/out not 8-byte aligned");
         if (ranges_overlap(in, out, sizeof(float2) * (size_t)nvalid))
             return fail(VBW_ERR_INVALID_ARG, "in and out overlap");
         vbw_status st = launch_stream_range(s, (const float2*)in, (float2*)out, 1, nvalid, false);
@@ -732,6 +742,8 @@ static void batch_free(vbw_batch_s* bt)
         cudaFree(G.d_jobs);
         cudaFree(G.d_tiles);
     }
+    for (auto* z : bt->d_zjobs) cudaFree(z);
+    cudaFree(bt->d_zmjobs);
     cudaFree(bt->d_mjobs);
     cudaFree(bt->d_mtiles);
     cudaFree(bt->d_bands);
@@ -765,6 +777,8 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
         if (g.nsamples < 0) return fail(VBW_ERR_INVALID_ARG, "signal %d: nsamples < 0", i);
         if (g.nsamples > 0 && (!g.in || !g.out))
             return fail(VBW_ERR_INVALID_ARG, "signal %d: in/out is NULL", i);
+        if (g.nsamples > 0 && (misaligned(g.in) || misaligned(g.out)))
+            return fail(VBW_ERR_INVALID_ARG, "signal %d: in/out not 8-byte aligned", i);
         if (g.nsamples > 0 && ranges_overlap(g.in, g.out, sizeof(float2) * (size_t)g.nsamples))
             return fail(VBW_ERR_INVALID_ARG, "signal %d: in and out overlap", i);
         const int64_t nb = (g.nsamples + g.plan->M - 1) / g.plan->M;
@@ -901,15 +915,16 @@ extern "C" vbw_status vbw_batch_set_mode(vbw_batch_t bt, int mode, double mixed_
 }
 
 static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t1, cudaStream_t st,
-                                      int max_ctas = 0)
+                                      int max_ctas = 0, const OlsJob* jobs = nullptr, int flags = 0)
 {
     vbw_plan_s* p = G.plan;
     OlsArgs a;
     memset(&a, 0, sizeof(a));
-    a.jobs = G.d_jobs;
+    a.jobs = jobs ? jobs : G.d_jobs;
     a.tiles = G.d_tiles + t0;
     a.ntiles = t1 - t0;
     fill_plan_args(a, p);
+    a.flags = flags;
     return launch_fp32(p->N, a, p->sms, st, max_ctas);
 }
 
@@ -917,15 +932,18 @@ static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t
 // order. MIXED: one persistent launch over every mixable plan, with the remaining plans (N = 2048
 // or other overlaps) launched beside it on a forked stream; the SMs are shared in proportion to
 // the transform work unless a share was set. AUTO: MIXED when at least two plans mix.
-static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st)
+static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st, bool zero_copy = false)
 {
     int launches = 0;
+    const int flags = zero_copy ? kOlsNoBulk : 0;
     const bool use_mixed = bt->mode == VBW_BATCH_MIXED
                                ? !bt->mixed_groups.empty()
                                : (bt->mode == VBW_BATCH_AUTO && bt->mixed_groups.size() >= 2);
     if (!use_mixed) {
-        for (auto& G : bt->groups) {
-            cudaError_t e = launch_group_range(G, 0, G.ntiles, st);
+        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+            const BatchGroup& G = bt->groups[gi];
+            cudaError_t e = launch_group_range(G, 0, G.ntiles, st, 0,
+                                               zero_copy ? bt->d_zjobs[gi] : nullptr, flags);
             if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
             ++launches;
         }
@@ -955,6 +973,8 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st)
     MixedArgs ma = bt->margs;
     ma.wait_limit = g_wait_limit_debug ? 2000000LL : 0;
     ma.debug = g_wait_limit_debug ? 1 : 0;
+    ma.flags = flags;
+    if (zero_copy) ma.jobs = bt->d_zmjobs;
     int grid = 0;
     cudaError_t e = launch_ols_mixed(ma, 1024, mwarps, sms, mixed_per_sm * mixed_sms, st, &grid);
     if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "mixed launch failed: %s", cudaGetErrorString(e));
@@ -966,7 +986,8 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st)
                 continue;
             const BatchGroup& G = bt->groups[gi];
             const int per_sm = G.plan->N >= 2048 ? 2 : 4;
-            e = launch_group_range(G, 0, G.ntiles, bt->s_side, per_sm * side_sms);
+            e = launch_group_range(G, 0, G.ntiles, bt->s_side, per_sm * side_sms,
+                                   zero_copy ? bt->d_zjobs[gi] : nullptr, flags);
             if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
             ++launches;
         }
@@ -974,6 +995,75 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st)
         VBW_CUDA(cudaStreamWaitEvent(st, bt->ev_join, 0));
     }
     bt->last_launches = launches;
+    return VBW_OK;
+}
+
+// Device address of pinned host memory, or nullptr when p is not pinned (pageable memory).
+static const void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return at.devicePointer;
+}
+
+// Zero-copy run from pinned host memory: on a coherent CPU-GPU link (Grace-Blackwell NVLink-C2C)
+// the fused kernel reads its input from and writes its output to host memory directly, so nothing
+// is staged and the run is bound by the link instead of the copy engines. The kernels then use
+// plain loads and stores only (no TMA staging, no bulk prefetch). Returns VBW_ERR_UNSUPPORTED when
+// any buffer is not pinned (the caller then takes the staged path).
+static vbw_status batch_zero_copy(vbw_batch_s* bt, const void* const* host_in, void* const* host_out,
+                                  cudaStream_t st)
+{
+    const size_t n = bt->sigs.size();
+    std::vector<const void*> din(n), dout(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (bt->sigs[i].nsamples == 0) continue;
+        din[i] = mapped_host(host_in[i]);
+        dout[i] = mapped_host(host_out[i]);
+        if (!din[i] || !dout[i] || misaligned(din[i]) || misaligned(dout[i])) return VBW_ERR_UNSUPPORTED;
+    }
+    const bool same = bt->z_in.size() == n &&
+                      std::equal(din.begin(), din.end(), bt->z_in.begin()) &&
+                      std::equal(dout.begin(), dout.end(), bt->z_out.begin());
+    if (!same) {
+        // job arrays with the host addresses, same order as the device arrays
+        VBW_CUDA(cudaStreamSynchronize(st));
+        if (bt->d_zjobs.size() != bt->groups.size()) bt->d_zjobs.assign(bt->groups.size(), nullptr);
+        std::vector<std::vector<OlsJob>> zj(bt->groups.size());
+        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+            const BatchGroup& G = bt->groups[gi];
+            std::vector<OlsJob>& jobs = zj[gi];
+            jobs.resize(G.sig.size());
+            VBW_CUDA(cudaMemcpy(jobs.data(), G.d_jobs, sizeof(OlsJob) * jobs.size(), cudaMemcpyDeviceToHost));
+            for (size_t j = 0; j < jobs.size(); ++j) {
+                jobs[j].in = (const float2*)din[G.sig[j]];
+                jobs[j].out = (float2*)dout[G.sig[j]];
+            }
+            if (!bt->d_zjobs[gi]) VBW_CUDA(cudaMalloc(&bt->d_zjobs[gi], sizeof(OlsJob) * jobs.size()));
+            VBW_CUDA(cudaMemcpy(bt->d_zjobs[gi], jobs.data(), sizeof(OlsJob) * jobs.size(), cudaMemcpyHostToDevice));
+        }
+        if (bt->d_mjobs) {
+            // same order as the mixed array: mixed groups in order, their jobs in order; the
+            // mixed array numbers plans by mixed-group position
+            std::vector<OlsJob> mj;
+            for (size_t m = 0; m < bt->mixed_groups.size(); ++m)
+                for (OlsJob jj : zj[bt->mixed_groups[m]]) {
+                    jj.plan = (int32_t)m;
+                    mj.push_back(jj);
+                }
+            if (!bt->d_zmjobs) VBW_CUDA(cudaMalloc(&bt->d_zmjobs, sizeof(OlsJob) * mj.size()));
+            VBW_CUDA(cudaMemcpy(bt->d_zmjobs, mj.data(), sizeof(OlsJob) * mj.size(), cudaMemcpyHostToDevice));
+        }
+        bt->z_in = din;
+        bt->z_out = dout;
+    }
+    vbw_status s = batch_launch(bt, st, true);
+    if (s != VBW_OK) return s;
+    VBW_CUDA(cudaStreamSynchronize(st));
     return VBW_OK;
 }
 
@@ -995,6 +1085,10 @@ extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host
         VBW_CUDA(cudaEventCreateWithFlags(&bt->ev_done, cudaEventDisableTiming));
     }
     cudaStream_t user = (cudaStream_t)cuda_stream;
+    if (env_int("VBW_ZERO_COPY", 1) != 0 && !bt->sigs.empty()) {
+        vbw_status zs = batch_zero_copy(bt, host_in, host_out, user);
+        if (zs != VBW_ERR_UNSUPPORTED) return zs == VBW_OK ? ok() : zs;
+    }
     VBW_CUDA(cudaEventRecord(bt->ev_start, user));
     VBW_CUDA(cudaStreamWaitEvent(bt->s_h2d, bt->ev_start, 0));
     VBW_CUDA(cudaStreamWaitEvent(bt->s_comp, bt->ev_start, 0));
@@ -1011,10 +1105,20 @@ extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host
                 bytes += sizeof(float2) * (size_t)bt->sigs[G.sig[j1]].nsamples;
                 ++j1;
             }
-            for (int j = j0; j < j1; ++j) {
+            // one copy per run of signals that are contiguous on both sides
+            for (int j = j0; j < j1;) {
                 const vbw_signal& g = bt->sigs[G.sig[j]];
-                VBW_CUDA(cudaMemcpyAsync((void*)g.in, host_in[G.sig[j]], sizeof(float2) * g.nsamples,
-                                         cudaMemcpyHostToDevice, bt->s_h2d));
+                const char* hsrc = (const char*)host_in[G.sig[j]];
+                char* ddst = (char*)g.in;
+                size_t len = sizeof(float2) * (size_t)g.nsamples;
+                int k = j + 1;
+                while (k < j1 && (const char*)host_in[G.sig[k]] == hsrc + len &&
+                       (const char*)bt->sigs[G.sig[k]].in == ddst + len) {
+                    len += sizeof(float2) * (size_t)bt->sigs[G.sig[k]].nsamples;
+                    ++k;
+                }
+                if (len) VBW_CUDA(cudaMemcpyAsync(ddst, hsrc, len, cudaMemcpyHostToDevice, bt->s_h2d));
+                j = k;
             }
             VBW_CUDA(cudaEventRecord(bt->ev_h, bt->s_h2d));
             VBW_CUDA(cudaStreamWaitEvent(bt->s_comp, bt->ev_h, 0));
@@ -1023,10 +1127,19 @@ extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host
             ++launches;
             VBW_CUDA(cudaEventRecord(bt->ev_c, bt->s_comp));
             VBW_CUDA(cudaStreamWaitEvent(bt->s_d2h, bt->ev_c, 0));
-            for (int j = j0; j < j1; ++j) {
+            for (int j = j0; j < j1;) {
                 const vbw_signal& g = bt->sigs[G.sig[j]];
-                VBW_CUDA(cudaMemcpyAsync(host_out[G.sig[j]], g.out, sizeof(float2) * g.nsamples,
-                                         cudaMemcpyDeviceToHost, bt->s_d2h));
+                char* hdst = (char*)host_out[G.sig[j]];
+                const char* dsrc = (const char*)g.out;
+                size_t len = sizeof(float2) * (size_t)g.nsamples;
+                int k = j + 1;
+                while (k < j1 && (char*)host_out[G.sig[k]] == hdst + len &&
+                       (const char*)bt->sigs[G.sig[k]].out == dsrc + len) {
+                    len += sizeof(float2) * (size_t)bt->sigs[G.sig[k]].nsamples;
+                    ++k;
+                }
+                if (len) VBW_CUDA(cudaMemcpyAsync(hdst, dsrc, len, cudaMemcpyDeviceToHost, bt->s_d2h));
+                j = k;
             }
             j0 = j1;
         }

@@ -127,8 +127,10 @@ struct OlsArgs {
     int* status;          // device status word (bit flags, e.g. a bounded wait that gave up) or nullptr
     int64_t wait_limit;   // bound of device-side waits in SM cycles (0 = default, about 2 s)
     int32_t debug;        // test hook, bit 0: skip the staging copies (their waits then run out)
-    int32_t pad_;
+    int32_t flags;        // kOlsNoBulk: signals live in host memory, use plain loads and stores only
 };
+
+constexpr int kOlsNoBulk = 1;
 
 // One plan of a mixed-plan launch (overlap N/4).
 struct MixedPlan {
@@ -152,6 +154,8 @@ struct MixedArgs {
     int32_t debug;        // as OlsArgs::debug
     int* status;
     int64_t wait_limit;   // as OlsArgs::wait_limit
+    int32_t flags;        // as OlsArgs::flags
+    int32_t pad2_;
 };
 
 }  // namespace vbw

@@ -160,3 +160,70 @@ def test_tune_set_changes_shape_not_result(cuda):
         vbw.vbw_tune_set(300, 4)
     with pytest.raises(vbw.VbwError):
         vbw.vbw_tune_set(512, 6)
+
+
+def test_signals_at_odd_offsets_of_one_buffer(cuda):
+    """Signals packed back to back in one device buffer start at arbitrary sample offsets, so
+    some are only 8-byte aligned: the bulk L2 prefetch and the TMA staging must skip (or realign)
+    those, and the results must not change. Also covers vbw_batch_run_host on packed buffers."""
+    torch = cuda
+    w = wl.mixed(seed=21, nstreams=30, log2_lo=11.0, log2_hi=14.5)
+    lens = [len(s.x) for s in w.signals]
+    offs = np.concatenate([[1], 1 + np.cumsum(lens)])         # odd start: every base shifts
+    assert any(o % 2 for o in offs[:-1])
+    total = int(offs[-1]) + 1
+    host = np.zeros(total, np.complex64)
+    for s, o in zip(w.signals, offs):
+        host[o:o + len(s.x)] = s.x
+    d_in = torch.from_numpy(host).cuda()
+    d_out = torch.full_like(d_in, float("nan"))
+    plans = {N: vbw.Plan(N, N // 4, w.V) for N in (128, 256, 512, 1024, 2048)}
+    rows = [(plans[s.N], d_in[o:o + len(s.x)], d_out[o:o + len(s.x)], s.band)
+            for s, o in zip(w.signals, offs)]
+    b = vbw.Batch(rows)
+    for mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_MIXED):
+        d_out.fill_(float("nan"))
+        b.set_mode(mode)
+        b.run()
+        torch.cuda.synchronize()
+        y = d_out.cpu().numpy()
+        for s, o in zip(w.signals, offs):
+            assert_parity(y[o:o + len(s.x)], oracle.filter(s.N, s.overlap, w.V, s.band, s.x),
+                          what=f"stream {s.stream} offset {o}")
+    hout = np.zeros_like(host)
+    b.run_host([host[o:o + len(s.x)] for s, o in zip(w.signals, offs)],
+               [hout[o:o + len(s.x)] for s, o in zip(w.signals, offs)])
+    for s, o in zip(w.signals, offs):
+        np.testing.assert_array_equal(hout[o:o + len(s.x)], y[o:o + len(s.x)])
+
+
+def test_misaligned_pointer_is_rejected(cuda):
+    torch = cuda
+    plan = vbw.Plan(256, 64, wl.transition_table(1, 6))
+    buf = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    s = vbw.Stream(plan, 10)
+    with pytest.raises(vbw.VbwError) as e:
+        vbw.vbw_filter(s.handle, buf.data_ptr() + 4, buf[2048:].data_ptr(), 1)
+    assert e.value.code == 1
+
+
+def test_run_host_zero_copy_matches_device_path(cuda):
+    """Pinned host buffers: the kernels work on host memory directly (zero copy); pageable
+    buffers: staged copies. Both give the device path's output bit for bit."""
+    torch = cuda
+    w, plans, xs, ys, b = mixed_batch(torch, nstreams=20, seed=12)
+    b.run()
+    torch.cuda.synchronize()
+    dev = [y.cpu().numpy() for y in ys]
+    for mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_MIXED):
+        b.set_mode(mode)
+        hin = [torch.from_numpy(s.x).pin_memory() for s in w.signals]
+        hout = [torch.zeros_like(h).pin_memory() for h in hin]
+        b.run_host([h.numpy() for h in hin], [h.numpy() for h in hout])
+        for a, h in zip(dev, hout):
+            np.testing.assert_array_equal(a, h.numpy())
+        pin = [np.ascontiguousarray(s.x) for s in w.signals]
+        pout = [np.zeros_like(p) for p in pin]
+        b.run_host(pin, pout)
+        for a, h in zip(dev, pout):
+            np.testing.assert_array_equal(a, h)
