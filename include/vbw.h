@@ -183,6 +183,33 @@ vbw_status vbw_debug_set(int flags);
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */
 vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
 
+/* Filters one whole signal without allocating anything. This is for callers that cannot
+ * allocate device memory: a host framework that owns every device allocation through its own
+ * pool, a real-time loop that cannot afford cudaMalloc's device synchronization and latency, or
+ * code that must not touch the CUDA allocator at all. The paper has no counterpart; it is a
+ * deployment convenience.
+ *
+ * Behaviour: as a batch of one signal (zero history, final partial block zero padded), with plan
+ * geometry (N, overlap, L_V = transition samples, host doubles read during the call) and band
+ * k1, on cuda_stream (a cudaStream_t, NULL = legacy stream). The caller passes device complex64
+ * `in` and `out` of nsamples samples (8-byte aligned, not overlapping). The twiddle rows, the
+ * float32 transition table and the kernel's status word live in one fixed 64 KiB array of device
+ * memory that belongs to the library image. Every GPU that loads the library holds it until the
+ * process exits.
+ *
+ * The first call on a device looks up that array's device address, with the device current. Make
+ * that first call before any stream capture. Every call shares the array and rewrites its tables,
+ * so calls that overlap on the GPU race: order them on one stream, or synchronize between them.
+ * The call itself makes no cudaMalloc/cudaFree and calls no allocating library routine. Requests
+ * beyond the array's capacity are rejected with VBW_ERR_INVALID_ARG; every geometry vbw_plan
+ * accepts fits.
+ *
+ * Errors: VBW_ERR_INVALID_ARG, VBW_ERR_BAND_RANGE, VBW_ERR_CUDA. Device-side wait timeouts are not
+ * reported by this call. */
+vbw_status vbw_filter_static(int N, int overlap, const double* transition_samples, int L_V,
+                             int band, const void* in, void* out, int64_t nsamples,
+                             void* cuda_stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* vbw_last_error(void);
 

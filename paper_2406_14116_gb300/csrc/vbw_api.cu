@@ -59,6 +59,14 @@ static vbw_status ok()
     return VBW_OK;
 }
 
+namespace vbw {
+vbw_status set_error(vbw_status st, const char* msg)
+{
+    g_last_error = msg;
+    return st;
+}
+}  // namespace vbw
+
 extern "C" const char* vbw_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char* vbw_version(void) { return "libvbw 0.1 (sm_103a)"; }
 

@@ -1,0 +1,148 @@
+// vbw_filter_static: whole-signal OLS VBW filtering that allocates nothing.
+//
+// Some callers cannot allocate device memory. A host framework may own every device allocation
+// through its own pool. A real-time loop cannot afford cudaMalloc's implicit device
+// synchronization and unbounded latency. Code may run where the CUDA allocator must not be
+// touched. The usual path needs a plan (its twiddle rows and transition table live in memory
+// that vbw_plan allocates). This entry point keeps those tables, and the kernel's status word, in
+// one fixed array of device memory that is part of the library image. Every GPU that loads the
+// library holds that array until the process exits.
+//
+// The kernel is the same fused FP32 kernel as every other path (ols_fp32_kernel, single-job form).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "ols_fp32.cuh"
+#include "vbw.h"
+
+// Plan-time table kernels of vbw_api.cu.
+__global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E);
+__global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV);
+
+namespace vbw {
+template <int N>
+cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
+                            int* grid_out);
+vbw_status set_error(vbw_status st, const char* msg);   // vbw_last_error() text (vbw_api.cu)
+}  // namespace vbw
+
+namespace {
+
+// Layout of the scratch (bytes). Sized for the largest plan the library accepts (N = 2048,
+// L_V = N/2 - 2), so every valid request fits.
+constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 float2 = 16896 bytes
+constexpr size_t kTwCap = 32768;
+constexpr size_t kVOff = kTwOff + kTwCap;    // transition table, float32: at most 4088 bytes
+constexpr size_t kVCap = 8192;
+constexpr size_t kVdOff = kVOff + kVCap;     // transition table as passed (double): <= 8176 bytes
+constexpr size_t kVdCap = 8192;
+constexpr size_t kStatusOff = kVdOff + kVdCap;   // device status word of the kernel
+constexpr size_t kScratchBytes = 64 * 1024;      // the whole array: 64 KiB per GPU
+static_assert(kStatusOff + sizeof(int) <= kScratchBytes, "scratch layout exceeds the array");
+
+static __device__ __align__(256) unsigned char vbw_static_scratch[kScratchBytes];
+
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch[kMaxDevices] = {};   // device address of the scratch, per device
+
+vbw_status fail_static(vbw_status st, const char* msg) { return vbw::set_error(st, msg); }
+
+// Device address of this device's scratch. The first call on a device looks it up, with the
+// device current; later calls reuse it.
+vbw_status scratch_address(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail_static(VBW_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, vbw_static_scratch);
+        if (e != cudaSuccess || !p) return fail_static(VBW_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+        g_scratch[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_scratch[dev];
+    return VBW_OK;
+}
+
+int layout_T_of(int N) { return vbw::layout_T(N); }
+
+}  // namespace
+
+extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int LV, int band,
+                                        const void* in, void* out, int64_t nsamples,
+                                        void* cuda_stream)
+{
+    using namespace vbw;
+    if (N < 128 || N > 2048 || (N & (N - 1)))
+        return fail_static(VBW_ERR_INVALID_ARG, "N must be a power of two in [128, 2048]");
+    if (overlap <= 0 || overlap >= N || (overlap & 1))
+        return fail_static(VBW_ERR_INVALID_ARG, "overlap must be even and in (0, N)");
+    if (LV < 1 || LV > N / 2 - 2) return fail_static(VBW_ERR_INVALID_ARG, "L_V must be in [1, N/2-2]");
+    if (!V) return fail_static(VBW_ERR_INVALID_ARG, "transition_samples is NULL");
+    if (band < 1 || band > N / 2 - LV - 1) return fail_static(VBW_ERR_BAND_RANGE, "band outside [1, N/2-L_V-1]");
+    if (nsamples < 0) return fail_static(VBW_ERR_INVALID_ARG, "nsamples < 0");
+    const int T = layout_T_of(N), E = N / T;
+    const size_t tw_bytes = sizeof(float2) * (size_t)T * (E + 2);
+    if (tw_bytes > kTwCap || sizeof(float) * (size_t)LV > kVCap || sizeof(double) * (size_t)LV > kVdCap)
+        return fail_static(VBW_ERR_INVALID_ARG, "request exceeds the static scratch (64 KiB)");
+    if (nsamples == 0) return vbw::set_error(VBW_OK, "");
+    if (!in || !out) return fail_static(VBW_ERR_INVALID_ARG, "in/out is NULL");
+    if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
+        return fail_static(VBW_ERR_INVALID_ARG, "in/out not 8-byte aligned");
+    {
+        const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out, n = sizeof(float2) * (uintptr_t)nsamples;
+        if (a < b + n && b < a + n) return fail_static(VBW_ERR_INVALID_ARG, "in and out overlap");
+    }
+
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail_static(VBW_ERR_CUDA, "no usable CUDA device");
+    unsigned char* scratch = nullptr;
+    vbw_status st = scratch_address(dev, &scratch);
+    if (st != VBW_OK) return st;
+    float2* tw = reinterpret_cast<float2*>(scratch + kTwOff);
+    float* Vf = reinterpret_cast<float*>(scratch + kVOff);
+    double* Vd = reinterpret_cast<double*>(scratch + kVdOff);
+    int* status = reinterpret_cast<int*>(scratch + kStatusOff);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    // tables of this call (every call rewrites them), status word cleared
+    if (cudaMemcpyAsync(Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
+        return fail_static(VBW_ERR_CUDA, "table upload failed");
+    const int tw_entries = T * (E + 2);
+    vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
+    vbw_round_table_kernel<<<(LV + 255) / 256, 256, 0, s>>>(Vd, Vf, LV);
+    if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
+
+    OlsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.job.in = static_cast<const float2*>(in);
+    a.job.out = static_cast<float2*>(out);
+    a.job.nsamp = nsamples;
+    a.job.band0 = band;
+    const int64_t M = N - overlap;
+    const int64_t nblocks = (nsamples + M - 1) / M;
+    const int B = 32 / T;
+    a.ntiles = (nblocks + B - 1) / B;
+    a.tw = tw;
+    a.V = Vf;
+    a.overlap = overlap;
+    a.LV = LV;
+    a.status = status;
+    const int warps = (N <= 1024) ? 8 : 4;
+    int grid = 0;
+    cudaError_t e;
+    switch (N) {
+    case 128: e = launch_ols_fp32<128>(a, warps, sms, 0, s, &grid); break;
+    case 256: e = launch_ols_fp32<256>(a, warps, sms, 0, s, &grid); break;
+    case 512: e = launch_ols_fp32<512>(a, warps, sms, 0, s, &grid); break;
+    case 1024: e = launch_ols_fp32<1024>(a, warps, sms, 0, s, &grid); break;
+    default: e = launch_ols_fp32<2048>(a, warps, sms, 0, s, &grid); break;
+    }
+    if (e != cudaSuccess) return fail_static(VBW_ERR_CUDA, "filter launch failed");
+    return vbw::set_error(VBW_OK, "");
+}

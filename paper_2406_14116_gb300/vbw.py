@@ -84,6 +84,7 @@ def lib():
         "vbw_tune_set": [i32, i32, i32],
         "vbw_plan_status": [p, p, i32],
         "vbw_debug_set": [i32],
+        "vbw_filter_static": [i32, i32, p, i32, i32, p, p, i64, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -276,6 +277,14 @@ def vbw_plan_status_raw(plan: int, clear: bool = False) -> tuple[int, int]:
 
 def vbw_debug_set(flags: int):
     _check(lib().vbw_debug_set(flags))
+
+
+def vbw_filter_static(N: int, overlap: int, transition_samples, band: int, inp, out,
+                      nsamples: int, cuda_stream=None):
+    """Whole-signal filtering that allocates nothing (tables in the library's static scratch)."""
+    V = np.ascontiguousarray(np.asarray(transition_samples, dtype=np.float64))
+    _check(lib().vbw_filter_static(N, overlap, _host_ptr(V), len(V), band, _dev_ptr(inp),
+                                   _dev_ptr(out), nsamples, _stream_handle(cuda_stream)))
 
 
 def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
