@@ -23,7 +23,6 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
-import glob
 import hashlib
 import json
 import os
@@ -66,11 +65,14 @@ def parse_args():
     return ap.parse_args()
 
 
+KERNEL_SOURCES = ("ols_fp32.cuh", "fft_reg.cuh", "vbw_common.cuh")   # the fused FP32 kernel
+
+
 def source_hash() -> str:
+    """Hash of the sources that define the fused FP32 kernel (profiles record it)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2406_14116_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2406_14116_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
 
