@@ -53,7 +53,16 @@ typedef enum {
     VBW_ERR_UNSUPPORTED = 8  /* valid request that this build does not provide              */
 } vbw_status;
 
-enum { VBW_PREC_FP32 = 0 };
+/* Arithmetic of a plan's DFT stages:
+ *   VBW_PREC_FP32          FP32 register/shared-memory FFT on the CUDA cores (any N, any overlap);
+ *   VBW_PREC_BF16_SPLIT    DFT-matrix GEMMs on the tensor cores (tcgen05), operands split into
+ *                          bfloat16 hi + lo, products hi*hi + hi*lo + lo*hi, FP32 accumulation;
+ *   VBW_PREC_FP16_SCALED   the same with float16 hi + lo pieces of each data row scaled into
+ *                          (-1, 1) by a power of two (scaled back exactly after the product);
+ *   VBW_PREC_BF16_SPLIT3   bfloat16 hi + mid + lo, six products.
+ * The tensor-core precisions take N in {256, 512} with overlap N/4 (VBW_ERR_UNSUPPORTED otherwise).
+ * The DFT matrices and twiddles are generated in FP64 on the GPU at plan time, then split. */
+enum { VBW_PREC_FP32 = 0, VBW_PREC_BF16_SPLIT = 1, VBW_PREC_FP16_SCALED = 2, VBW_PREC_BF16_SPLIT3 = 3 };
 
 /* Creates a plan for N-point OLS with the given overlap and the L_V transition samples
  * V(0..L_V-1) of eq. (FS_Hk_real) (host array, read during the call; any finite values, the
@@ -178,6 +187,12 @@ vbw_status vbw_plan_status(vbw_plan_t plan, int* flags, int clear);
  * without issuing their copies and shortens the device wait limit to about a millisecond, so the
  * bounded waits run out, set the status word and stop the warp, with no fault. 0 turns it off. */
 vbw_status vbw_debug_set(int flags);
+
+/* Test hook: D (128 x NN) = A (128 x K) B (K x NN) on the tensor cores through the operand
+ * layout, descriptors, TMEM accumulator and waits the tensor-core OLS kernel uses, with A and B
+ * rounded once to bfloat16 (bf16 != 0) or float16. K, NN in {32, 64}; host float arrays,
+ * row-major. Synchronous; allocates. */
+vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A, const float* B, float* D);
 
 /* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */

@@ -61,15 +61,19 @@ __host__ __device__ inline size_t ols_smem_bytes(int warps)
 // g(kk) = H_R / N with H_R of eq. (FS_Hk_real) on the non-negative half, kk = 0..N/2:
 // kk <= k1 - 1 passband (1), k1 <= kk <= k1 + L_V - 1 transition (V(kk - k1)), else stopband (0).
 // 1/N is a power of two, so g * N recovers H_R exactly. Written by the T lanes of one lane group.
+// H_R at the non-negative bin kk (0 <= kk <= N/2) for band k1: 1, V(kk - k1) or 0.
+__device__ __forceinline__ float hr_gain(int kk, int k1, int LV, const float* V)
+{
+    const int r = kk - k1;
+    return r < 0 ? 1.f : (r < LV ? V[r] : 0.f);
+}
+
 template <int N>
 __device__ __forceinline__ void build_gains(float* gtab, int t, int k1, int LV, const float* V)
 {
     constexpr int T = OlsGeom<N>::T;
     constexpr float inv_n = 1.0f / N;
-    for (int kk = t; kk <= N / 2; kk += T) {
-        const int r = kk - k1;
-        gtab[kk] = (r < 0 ? 1.f : (r < LV ? V[r] : 0.f)) * inv_n;
-    }
+    for (int kk = t; kk <= N / 2; kk += T) gtab[kk] = hr_gain(kk, k1, LV, V) * inv_n;
 }
 
 // L2 prefetch of a contiguous byte range with one bulk-copy instruction (16-byte aligned start,

@@ -26,6 +26,10 @@ cudaError_t launch_export_hr(const float* V, int LV, int k1, float* out, cudaStr
 cudaError_t launch_ols_mixed(const MixedArgs& a, int maxn, int warps, int sms, int max_ctas,
                              cudaStream_t st, int* grid_out);
 size_t ols_warp_bytes(int N);
+cudaError_t launch_ols_tc(int N, int prec, const OlsArgs& a, int sms, cudaStream_t st);
+size_t tc_table_bytes(int N, int prec);
+cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st);
+constexpr int kTcTileBlocks = 8;
 }  // namespace vbw
 
 using namespace vbw;
@@ -107,7 +111,11 @@ struct vbw_plan_s {
     float2* d_tw = nullptr;
     float* d_V = nullptr;
     int* d_status = nullptr;   // device status word of this plan's launches (bit flags)
+    unsigned char* d_tc = nullptr;   // tensor-core precisions: DFT-matrix pieces and twiddles
 };
+
+// Blocks per work tile: one warp-tile of the FP32 kernel, or the 8-block tile of the tensor-core one.
+static int tile_blocks(const vbw_plan_s* p);
 
 struct vbw_stream_s {
     vbw_plan_s* plan = nullptr;
@@ -257,9 +265,22 @@ static void fill_plan_args(OlsArgs& a, const vbw_plan_s* p)
     a.status = p->d_status;
     a.wait_limit = g_wait_limit_debug ? 2000000LL : 0;
     a.debug = g_wait_limit_debug ? 1 : 0;
+    a.tc_tables = p->d_tc;
+}
+
+// Launch of plan p's kernel: the fused FP32 kernel, or the tensor-core one.
+static cudaError_t launch_plan(const vbw_plan_s* p, const OlsArgs& a, cudaStream_t st, int max_ctas = 0)
+{
+    if (p->prec != VBW_PREC_FP32) return launch_ols_tc(p->N, p->prec, a, p->sms, st);
+    return launch_fp32(p->N, a, p->sms, st, max_ctas);
 }
 
 static int blocks_per_warp(int N) { return 32 / layout_T(N); }
+
+static int tile_blocks(const vbw_plan_s* p)
+{
+    return p->prec == VBW_PREC_FP32 ? blocks_per_warp(p->N) : kTcTileBlocks;
+}
 
 // entries of the per-plan twiddle table: T rows of E + 2 (see OlsGeom::TW)
 static int twiddle_entries(int N) { return layout_T(N) * (N / layout_T(N) + 2); }
@@ -281,8 +302,10 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
     if (!V) return fail(VBW_ERR_INVALID_ARG, "transition_samples is NULL");
     for (int i = 0; i < LV; ++i)
         if (!std::isfinite(V[i])) return fail(VBW_ERR_INVALID_ARG, "V[%d] is not finite", i);
-    if (precision != VBW_PREC_FP32)
+    if (precision < VBW_PREC_FP32 || precision > VBW_PREC_BF16_SPLIT3)
         return fail(VBW_ERR_INVALID_ARG, "precision %d is not a known precision", precision);
+    if (precision != VBW_PREC_FP32 && !((N == 256 || N == 512) && overlap == N / 4))
+        return fail(VBW_ERR_UNSUPPORTED, "tensor-core precisions need N in {256, 512} and overlap N/4");
 
     vbw_plan_s* p = new (std::nothrow) vbw_plan_s();
     if (!p) return fail(VBW_ERR_NOMEM, "host allocation failed");
@@ -317,6 +340,17 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
         }
         vbw_twiddle_kernel<<<(twiddle_entries(N) + 255) / 256, 256>>>(p->d_tw, N, layout_T(N),
                                                                        N / layout_T(N));
+        if (precision != VBW_PREC_FP32) {
+            if (cudaMalloc(&p->d_tc, tc_table_bytes(N, precision)) != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(VBW_ERR_NOMEM, "device allocation for the tensor-core tables failed");
+                break;
+            }
+            if ((e = build_tc_table(N, precision, p->d_tc, 0)) != cudaSuccess) {
+                st = fail(VBW_ERR_CUDA, "tensor-core table kernel failed: %s", cudaGetErrorString(e));
+                break;
+            }
+        }
         vbw_round_table_kernel<<<(LV + 255) / 256, 256>>>(d_Vd, p->d_V, LV);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
             st = fail(VBW_ERR_CUDA, "plan table kernels failed: %s", cudaGetErrorString(e));
@@ -328,6 +362,7 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_V) cudaFree(p->d_V);
         if (p->d_status) cudaFree(p->d_status);
+        if (p->d_tc) cudaFree(p->d_tc);
         delete p;
         return st;
     }
@@ -341,6 +376,7 @@ extern "C" vbw_status vbw_plan_destroy(vbw_plan_t p)
     cudaFree(p->d_tw);
     cudaFree(p->d_V);
     cudaFree(p->d_status);
+    cudaFree(p->d_tc);
     delete p;
     return ok();
 }
@@ -517,10 +553,10 @@ static vbw_status launch_stream_range(vbw_stream_s* s, const float2* in, float2*
         ++nchg;
     }
     a.nchg = nchg;
-    const int B = blocks_per_warp(p->N);
+    const int B = tile_blocks(p);
     a.ntiles = (nb + B - 1) / B;
     fill_plan_args(a, p);
-    cudaError_t e = launch_fp32(p->N, a, p->sms, s->st);
+    cudaError_t e = launch_plan(p, a, s->st);
     if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "filter launch failed: %s", cudaGetErrorString(e));
     if (keep_tail) s->cur ^= 1;
     s->pos += nb;
@@ -770,7 +806,10 @@ static cudaError_t upload(T** dst, const std::vector<T>& v)
 
 // Plans a mixed launch can take: overlap N/4 and N <= 1024 (N = 2048 keeps its own kernel, whose
 // register and shared-memory footprint would otherwise apply to every N).
-static bool mixable(const vbw_plan_s* p) { return p->O == p->N / 4 && p->N <= 1024; }
+static bool mixable(const vbw_plan_s* p)
+{
+    return p->prec == VBW_PREC_FP32 && p->O == p->N / 4 && p->N <= 1024;
+}
 
 extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t* out)
 {
@@ -832,7 +871,7 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
     int32_t tw_off = 0;
     for (auto& kv : by_plan) {
         vbw_plan_s* p = kv.first;
-        const int B = blocks_per_warp(p->N);
+        const int B = tile_blocks(p);
         const bool mix = mixable(p) && nmixed < kMaxMixedPlans;
         const int plan_idx = mix ? nmixed : 0;
         std::vector<OlsJob> jobs;
@@ -933,7 +972,7 @@ static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t
     a.ntiles = t1 - t0;
     fill_plan_args(a, p);
     a.flags = flags;
-    return launch_fp32(p->N, a, p->sms, st, max_ctas);
+    return launch_plan(p, a, st, max_ctas);
 }
 
 // Device-side run of a prepared batch. PER_PLAN: one full-GPU persistent launch per plan, in

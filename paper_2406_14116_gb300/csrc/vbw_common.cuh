@@ -128,6 +128,7 @@ struct OlsArgs {
     int64_t wait_limit;   // bound of device-side waits in SM cycles (0 = default, about 2 s)
     int32_t debug;        // test hook, bit 0: skip the staging copies (their waits then run out)
     int32_t flags;        // kOlsNoBulk: signals live in host memory, use plain loads and stores only
+    const unsigned char* tc_tables;   // tensor-core plans: DFT-matrix pieces and twiddles
 };
 
 constexpr int kOlsNoBulk = 1;

@@ -24,7 +24,7 @@ VBW_OK = 0
 STATUS_NAMES = {0: "VBW_OK", 1: "VBW_ERR_INVALID_ARG", 2: "VBW_ERR_BAND_RANGE", 3: "VBW_ERR_NOMEM",
                 4: "VBW_ERR_CUDA", 5: "VBW_ERR_TIMEOUT", 6: "VBW_ERR_BUSY", 7: "VBW_ERR_STATE",
                 8: "VBW_ERR_UNSUPPORTED"}
-VBW_PREC_FP32 = 0
+VBW_PREC_FP32, VBW_PREC_BF16_SPLIT, VBW_PREC_FP16_SCALED, VBW_PREC_BF16_SPLIT3 = 0, 1, 2, 3
 VBW_BATCH_AUTO, VBW_BATCH_PER_PLAN, VBW_BATCH_MIXED = 0, 1, 2
 
 
@@ -85,6 +85,7 @@ def lib():
         "vbw_plan_status": [p, p, i32],
         "vbw_debug_set": [i32],
         "vbw_filter_static": [i32, i32, p, i32, i32, p, p, i64, p],
+        "vbw_debug_tc_gemm": [i32, i32, i32, p, p, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -285,6 +286,16 @@ def vbw_filter_static(N: int, overlap: int, transition_samples, band: int, inp, 
     V = np.ascontiguousarray(np.asarray(transition_samples, dtype=np.float64))
     _check(lib().vbw_filter_static(N, overlap, _host_ptr(V), len(V), band, _dev_ptr(inp),
                                    _dev_ptr(out), nsamples, _stream_handle(cuda_stream)))
+
+
+def vbw_debug_tc_gemm(A: np.ndarray, B: np.ndarray, bf16: bool = True) -> np.ndarray:
+    """D = A B on the tensor cores (A 128 x K, B K x NN, float32 host arrays)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    D = np.empty((A.shape[0], B.shape[1]), dtype=np.float32)
+    _check(lib().vbw_debug_tc_gemm(1 if bf16 else 0, A.shape[1], B.shape[1], _host_ptr(A),
+                                   _host_ptr(B), _host_ptr(D)))
+    return D
 
 
 def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
