@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--channels", type=int, default=None, help="channels / streams per GPU")
     ap.add_argument("--samples", type=int, default=None, help="samples per channel")
     ap.add_argument("--N", type=int, default=256, help="transform size of the precision workload")
+    ap.add_argument("--prec", choices=["fp32", "bf16", "fp16", "bf16x6"], default="fp32",
+                    help="DFT arithmetic: FP32 CUDA-core FFT, or tensor-core GEMMs with BF16 "
+                         "hi+lo, scaled FP16 hi+lo, or BF16 hi+mid+lo pieces")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -235,11 +238,19 @@ def make_streams(name, args, rank):
         nb = wl.nblocks_for(T, N, N // 4)
         streams = [Stream(N, N // 4, T, np.full(nb, int(k1[i]), np.int32), ("gauss", 4, i))
                    for i in range(n)]
-        cfg = {"workload": f"precision geometry, FP32 path: {n} x {T} complex64, N={N}, overlap "
-                           f"{N // 4}, k1~U{{1..N/2-13}}, L_V=12",
-               "channels": n, "samples_per_channel": T, "N": N, "seed": 4}
+        cfg = {"workload": f"precision: {n} x {T} complex64, N={N}, overlap {N // 4}, "
+                           f"k1~U{{1..N/2-13}}, L_V=12, DFT stages {PREC_NAME[args.prec]}",
+               "channels": n, "samples_per_channel": T, "N": N, "seed": 4,
+               "precision": PREC_NAME[args.prec]}
         return streams, V, cfg
     raise ValueError(name)
+
+
+PREC_CODE = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x6": 3}
+PREC_NAME = {"fp32": "FP32 register FFT (CUDA cores)",
+             "bf16": "tensor-core GEMMs, BF16 hi+lo (3 products), FP32 accumulation",
+             "fp16": "tensor-core GEMMs, row-scaled FP16 hi+lo (3 products), FP32 accumulation",
+             "bf16x6": "tensor-core GEMMs, BF16 hi+mid+lo (6 products), FP32 accumulation"}
 
 
 def gen_samples(gen, n):
@@ -408,7 +419,7 @@ def native_arm(args):
     for s in streams:
         key = (s.N, s.overlap)
         if key not in plans:
-            plans[key] = vbw.Plan(s.N, s.overlap, V)
+            plans[key] = vbw.Plan(s.N, s.overlap, V, precision=PREC_CODE[args.prec])
     batch = vbw.Batch([(plans[(s.N, s.overlap)], d_in[offs[i]:offs[i + 1]],
                         d_out[offs[i]:offs[i + 1]], s.band) for i, s in enumerate(streams)])
     side = torch.cuda.Stream()          # graphs cannot be captured on the default stream
@@ -525,13 +536,17 @@ def native_arm(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16x2 split, f32 acc", "fp16": "f16x2 scaled, f32 acc",
+                      "bf16x6": "bf16x3 split, f32 acc"}[args.prec],
+            "data": "synthetic",
             "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured"
                          else "fallback 6.8 TB/s",
-                         "kernel": "ols_fp32_kernel" if launches_per_step == 1 else "ols_fp32/ols_mixed kernels",
+                         "kernel": ("ols_tc_kernel (tcgen05)" if args.prec != "fp32" else
+                                    "ols_fp32_kernel" if launches_per_step == 1 else "ols_fp32/ols_mixed kernels"),
                          "launch_ms": step_ms / launches_per_step,
                          "step_ms": step_ms,
                          "algorithmic_bytes_per_step": BYTES_PER_SAMPLE * total},
@@ -540,7 +555,7 @@ def native_arm(args):
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
             "rms_rel_err_sampled": rms,
-            "rms_tol": FP32_RMS_TOL,
+            "rms_tol": FP32_RMS_TOL if args.prec == "fp32" else 1e-5,
         }
         if remeasured:
             line["remeasured_after_throttle"] = True
