@@ -225,6 +225,103 @@ vbw_status vbw_filter_static(int N, int overlap, const double* transition_sample
                              int band, const void* in, void* out, int64_t nsamples,
                              void* cuda_stream);
 
+/* ---- Serving: continuous batching of many live streams ----------------------------------------
+ *
+ * The paper filters one stream whose band changes at block boundaries (Sec. II, Sec. III-B). A
+ * serving deployment runs that filter on many independent streams at once, each sending chunks of
+ * any length at any time. The server keeps each stream's OLS state on the device (the O-sample
+ * tail and the fewer than M input samples that do not fill a block yet), merges the chunks queued
+ * at a moment into batches, and runs them through the fused kernels of the batch path.
+ *
+ * Chunks are admitted first in first out into one of `slots` batch slots, each an equal share of
+ * a device pool of `pool_bytes`. A batch takes chunks from the head of the queue while their input
+ * and output blocks fit its slot (admission by memory). A slot is free again once its batch's
+ * outputs are on the host. Up to `slots` batches are in flight, so one batch's copies overlap
+ * another's kernels.
+ *
+ * Semantics per stream. The output is the same as vbw_filter over the concatenated chunks,
+ * followed by vbw_flush at close, bit for bit, whatever other streams share the batches:
+ *   - a chunk's output is every block its samples complete: ((S + n) / M - S / M) * M samples,
+ *     with S the samples submitted before it. It is written to host_out from the stream's output
+ *     position floor(S / M) * M onward;
+ *   - a band change carried by a chunk (new_band >= 0) takes effect at block ceil(S / M), the first
+ *     block boundary at or after the chunk's first sample. Of several changes due at one block,
+ *     the last one submitted wins;
+ *   - vbw_server_close_stream emits the final partial block (S mod M samples, zero padded); the
+ *     stream slot can then be opened again.
+ * host_in must stay unchanged and host_out untouched until the chunk's completion is returned.
+ * Pinned host memory (cudaHostAlloc) gives asynchronous copies. Pageable memory works but is
+ * copied synchronously by the CUDA runtime.
+ *
+ * Threading: a server is not thread safe; one host thread drives it. */
+typedef struct vbw_server_s* vbw_server_t;
+
+typedef struct {
+    uint64_t tag;        /* the tag given at submit / close                                      */
+    int32_t stream;      /* stream index                                                         */
+    int32_t final_flush; /* 1 for the completion of vbw_server_close_stream                      */
+    int64_t produced;    /* output samples written to the chunk's host_out                       */
+    double t_submit;     /* vbw_server_clock() when the chunk was submitted                      */
+    double t_done;       /* vbw_server_clock() when the engine saw the chunk's outputs on the host */
+} vbw_completion;
+
+typedef struct {
+    int64_t queued;            /* chunks submitted, not yet admitted                             */
+    int64_t inflight_batches;  /* batches launched, not yet retired                              */
+    int64_t completions_ready; /* completions retired, not yet returned                          */
+    int64_t batches;           /* batches launched since creation                                */
+    int64_t launches;          /* kernel launches since creation                                 */
+    int64_t admitted;          /* chunks admitted since creation                                 */
+    int64_t slot_bytes;        /* device bytes per batch slot                                    */
+    int64_t slots;             /* batch slots                                                    */
+} vbw_server_stats;
+
+/* Creates a server for streams that use one of `plans` (all on the current device; the plans
+ * must outlive the server). max_streams: stream indices 0..max_streams-1; their state is
+ * allocated here (2 O + M samples each). pool_bytes: device memory for batch inputs and outputs,
+ * split into `slots` (1..64) equal slots.
+ * Errors: VBW_ERR_INVALID_ARG (a NULL plan, more than 64 plans, a slot smaller than 8 M samples),
+ * VBW_ERR_NOMEM. */
+vbw_status vbw_server_create(const vbw_plan_t* plans, int nplans, int max_streams, size_t pool_bytes,
+                             int slots, vbw_server_t* out);
+
+/* Waits for every batch in flight, then frees the server. Chunks still queued are dropped. */
+vbw_status vbw_server_destroy(vbw_server_t server);
+
+/* Opens stream index `stream` with plan plans[plan] and band k1 = band: zero history, position 0.
+ * Errors: VBW_ERR_INVALID_ARG, VBW_ERR_BAND_RANGE, VBW_ERR_STATE (the stream is open or closing). */
+vbw_status vbw_server_open_stream(vbw_server_t server, int stream, int plan, int band);
+
+/* Queues n input samples (host, complex64, 8-byte aligned) of an open stream. new_band: k1 from
+ * block ceil(S / M) on, or -1 for none. host_out: room for out_capacity samples, at least the
+ * chunk's output count (it may be NULL when that count is 0). tag comes back in the completion.
+ * Nothing runs until vbw_server_poll or vbw_server_wait.
+ * Errors: VBW_ERR_INVALID_ARG (bad pointer, too small an output, a chunk whose job cannot fit
+ * one slot), VBW_ERR_BAND_RANGE, VBW_ERR_STATE (stream not open, or closing). */
+vbw_status vbw_server_submit(vbw_server_t server, int stream, const void* host_in, int64_t n, int new_band,
+                             void* host_out, int64_t out_capacity, uint64_t tag);
+
+/* Queues the end of an open stream. Its completion carries the final partial block (S mod M
+ * samples, written to host_out) and final_flush = 1. The stream can be opened again after
+ * this call returns. Errors: VBW_ERR_INVALID_ARG (output too small), VBW_ERR_STATE. */
+vbw_status vbw_server_close_stream(vbw_server_t server, int stream, void* host_out, int64_t out_capacity,
+                                   uint64_t tag);
+
+/* Progresses the engine without blocking: retires finished batches, launches batches into free
+ * slots, and returns up to max_out completions (oldest first) in out[0 .. *nout). Completions come
+ * in submission order. Errors: VBW_ERR_INVALID_ARG, VBW_ERR_CUDA (a batch failed). */
+vbw_status vbw_server_poll(vbw_server_t server, vbw_completion* out, int max_out, int* nout);
+
+/* As vbw_server_poll, but if no completion is ready and a batch is in flight, blocks until the
+ * oldest batch finishes. Returns *nout = 0 only when nothing is queued or in flight. */
+vbw_status vbw_server_wait(vbw_server_t server, vbw_completion* out, int max_out, int* nout);
+
+/* Counters of the engine (see vbw_server_stats). */
+vbw_status vbw_server_info(vbw_server_t server, vbw_server_stats* out);
+
+/* The clock of t_submit / t_done: seconds of a monotonic host clock. */
+double vbw_server_clock(void);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* vbw_last_error(void);
 

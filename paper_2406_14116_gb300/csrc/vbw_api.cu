@@ -16,6 +16,7 @@
 
 #include "vbw.h"
 #include "vbw_common.cuh"
+#include "vbw_internal.h"
 
 namespace vbw {
 template <int N>
@@ -39,7 +40,7 @@ using namespace vbw;
 
 static thread_local std::string g_last_error;
 
-static vbw_status fail(vbw_status st, const char* fmt, ...)
+vbw_status fail(vbw_status st, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -57,7 +58,7 @@ static vbw_status fail(vbw_status st, const char* fmt, ...)
             return fail(VBW_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));        \
     } while (0)
 
-static vbw_status ok()
+vbw_status ok()
 {
     g_last_error.clear();
     return VBW_OK;
@@ -104,18 +105,6 @@ __global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV)
 // ------------------------------------------------------------------------------------------------
 // objects
 
-struct vbw_plan_s {
-    int N = 0, O = 0, M = 0, LV = 0, prec = 0;
-    int device = 0, sms = 0;
-    std::vector<double> V;
-    float2* d_tw = nullptr;
-    float* d_V = nullptr;
-    int* d_status = nullptr;   // device status word of this plan's launches (bit flags)
-    unsigned char* d_tc = nullptr;   // tensor-core precisions: DFT-matrix pieces and twiddles
-};
-
-// Blocks per work tile: one warp-tile of the FP32 kernel, or the 8-block tile of the tensor-core one.
-static int tile_blocks(const vbw_plan_s* p);
 
 struct vbw_stream_s {
     vbw_plan_s* plan = nullptr;
@@ -192,7 +181,7 @@ static int n_index(int N)
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-static vbw_status check_band(const vbw_plan_s* p, int band)
+vbw_status check_band(const vbw_plan_s* p, int band)
 {
     const int kmax = p->N / 2 - p->LV - 1;
     if (band < 1 || band > kmax)
@@ -202,7 +191,7 @@ static vbw_status check_band(const vbw_plan_s* p, int band)
 }
 
 // complex64 samples need 8-byte alignment
-static bool misaligned(const void* p) { return ((uintptr_t)p & 7) != 0; }
+bool misaligned(const void* p) { return ((uintptr_t)p & 7) != 0; }
 
 static bool ranges_overlap(const void* a, const void* b, size_t bytes)
 {
@@ -256,7 +245,7 @@ static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st
 }
 
 // Kernel arguments common to every launch of plan p.
-static void fill_plan_args(OlsArgs& a, const vbw_plan_s* p)
+void fill_plan_args(OlsArgs& a, const vbw_plan_s* p)
 {
     a.tw = p->d_tw;
     a.V = p->d_V;
@@ -269,7 +258,7 @@ static void fill_plan_args(OlsArgs& a, const vbw_plan_s* p)
 }
 
 // Launch of plan p's kernel: the fused FP32 kernel, or the tensor-core one.
-static cudaError_t launch_plan(const vbw_plan_s* p, const OlsArgs& a, cudaStream_t st, int max_ctas = 0)
+cudaError_t launch_plan(const vbw_plan_s* p, const OlsArgs& a, cudaStream_t st, int max_ctas)
 {
     if (p->prec != VBW_PREC_FP32) return launch_ols_tc(p->N, p->prec, a, p->sms, st);
     return launch_fp32(p->N, a, p->sms, st, max_ctas);
@@ -277,7 +266,7 @@ static cudaError_t launch_plan(const vbw_plan_s* p, const OlsArgs& a, cudaStream
 
 static int blocks_per_warp(int N) { return 32 / layout_T(N); }
 
-static int tile_blocks(const vbw_plan_s* p)
+int tile_blocks(const vbw_plan_s* p)
 {
     return p->prec == VBW_PREC_FP32 ? blocks_per_warp(p->N) : kTcTileBlocks;
 }

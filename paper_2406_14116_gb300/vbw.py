@@ -34,6 +34,13 @@ class VbwError(RuntimeError):
         self.code = code
 
 
+# vbw_completion / vbw_server_stats of include/vbw.h as numpy record types
+COMPLETION_DTYPE = np.dtype([("tag", "<u8"), ("stream", "<i4"), ("final_flush", "<i4"),
+                             ("produced", "<i8"), ("t_submit", "<f8"), ("t_done", "<f8")])
+SERVER_STATS_FIELDS = ("queued", "inflight_batches", "completions_ready", "batches", "launches",
+                       "admitted", "slot_bytes", "slots")
+
+
 class vbw_signal(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("nsamples", ctypes.c_int64), ("band", ctypes.c_int32),
@@ -86,6 +93,14 @@ def lib():
         "vbw_debug_set": [i32],
         "vbw_filter_static": [i32, i32, p, i32, i32, p, p, i64, p],
         "vbw_debug_tc_gemm": [i32, i32, i32, p, p, p],
+        "vbw_server_create": [p, i32, i32, sz, i32, pp],
+        "vbw_server_destroy": [p],
+        "vbw_server_open_stream": [p, i32, i32, i32],
+        "vbw_server_submit": [p, i32, p, i64, i32, p, i64, ctypes.c_uint64],
+        "vbw_server_close_stream": [p, i32, p, i64, ctypes.c_uint64],
+        "vbw_server_poll": [p, p, i32, p],
+        "vbw_server_wait": [p, p, i32, p],
+        "vbw_server_info": [p, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -95,6 +110,8 @@ def lib():
     L.vbw_last_error.restype = ctypes.c_char_p
     L.vbw_version.argtypes = []
     L.vbw_version.restype = ctypes.c_char_p
+    L.vbw_server_clock.argtypes = []
+    L.vbw_server_clock.restype = ctypes.c_double
     _lib = L
     return L
 
@@ -305,6 +322,65 @@ def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
     return out
 
 
+def _hptr(a) -> int:
+    """Address of a host buffer: a C-contiguous numpy array or a raw integer address."""
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    if not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous host array")
+    return int(a.ctypes.data)
+
+
+def vbw_server_create(plans, max_streams: int, pool_bytes: int, slots: int) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = ctypes.c_void_p()
+    _check(lib().vbw_server_create(arr, len(plans), max_streams, pool_bytes, slots, ctypes.byref(h)))
+    return h.value
+
+
+def vbw_server_destroy(sv: int):
+    _check(lib().vbw_server_destroy(sv))
+
+
+def vbw_server_open_stream(sv: int, stream: int, plan: int, band: int):
+    _check(lib().vbw_server_open_stream(sv, stream, plan, band))
+
+
+def vbw_server_submit(sv: int, stream: int, host_in, n: int, new_band: int, host_out,
+                      out_capacity: int, tag: int):
+    _check(lib().vbw_server_submit(sv, stream, _hptr(host_in), n, new_band, _hptr(host_out),
+                                   out_capacity, tag))
+
+
+def vbw_server_close_stream(sv: int, stream: int, host_out, out_capacity: int, tag: int):
+    _check(lib().vbw_server_close_stream(sv, stream, _hptr(host_out), out_capacity, tag))
+
+
+def vbw_server_poll(sv: int, out: np.ndarray) -> int:
+    """Fills out (COMPLETION_DTYPE records) from the front; returns how many."""
+    n = ctypes.c_int(0)
+    _check(lib().vbw_server_poll(sv, out.ctypes.data, len(out), ctypes.byref(n)))
+    return n.value
+
+
+def vbw_server_wait(sv: int, out: np.ndarray) -> int:
+    n = ctypes.c_int(0)
+    _check(lib().vbw_server_wait(sv, out.ctypes.data, len(out), ctypes.byref(n)))
+    return n.value
+
+
+def vbw_server_info(sv: int) -> dict:
+    v = (ctypes.c_int64 * len(SERVER_STATS_FIELDS))()
+    _check(lib().vbw_server_info(sv, v))
+    return dict(zip(SERVER_STATS_FIELDS, list(v)))
+
+
+def vbw_server_clock() -> float:
+    return float(lib().vbw_server_clock())
+
+
 # ---- handle holders ---------------------------------------------------------------------------
 
 class Plan:
@@ -404,6 +480,62 @@ class Batch:
     def close(self):
         if self.handle:
             vbw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server over ``plans`` (a list of Plan)."""
+
+    def __init__(self, plans, max_streams: int, pool_bytes: int, slots: int = 4,
+                 max_completions: int = 65536):
+        self.plans = list(plans)
+        self.handle = vbw_server_create([p.handle for p in self.plans], max_streams, pool_bytes, slots)
+        self._buf = np.zeros(max_completions, dtype=COMPLETION_DTYPE)
+
+    def open_stream(self, stream: int, plan: int, band: int):
+        vbw_server_open_stream(self.handle, stream, plan, band)
+
+    def submit(self, stream: int, host_in, n: int | None = None, new_band: int = -1, host_out=None,
+               out_capacity: int | None = None, tag: int = 0):
+        if n is None:
+            n = len(host_in)
+        if out_capacity is None:
+            out_capacity = 0 if host_out is None or isinstance(host_out, int) else len(host_out)
+        vbw_server_submit(self.handle, stream, host_in, n, new_band, host_out, out_capacity, tag)
+
+    def close_stream(self, stream: int, host_out=None, out_capacity: int | None = None, tag: int = 0):
+        if out_capacity is None:
+            out_capacity = 0 if host_out is None or isinstance(host_out, int) else len(host_out)
+        vbw_server_close_stream(self.handle, stream, host_out, out_capacity, tag)
+
+    def poll(self) -> np.ndarray:
+        return self._buf[:vbw_server_poll(self.handle, self._buf)].copy()
+
+    def wait(self) -> np.ndarray:
+        return self._buf[:vbw_server_wait(self.handle, self._buf)].copy()
+
+    def drain(self) -> np.ndarray:
+        """Runs until nothing is queued or in flight; returns every completion."""
+        got = []
+        while True:
+            c = self.wait()
+            if len(c) == 0:
+                break
+            got.append(c)
+        return np.concatenate(got) if got else np.zeros(0, dtype=COMPLETION_DTYPE)
+
+    def info(self) -> dict:
+        return vbw_server_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            vbw_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
