@@ -8,7 +8,8 @@ in HBM when the timed region starts and exceed L2 (2.1 GB read + 2.1 GB written 
 
 Other workloads (--workload): single (1 x 2^16, N=256; L2 flushed between steps), mixed (4096
 streams of mixed length and N in one batch, replayed as a CUDA graph), precision (16384 x 2^16,
-N = 256 or 512, FP32 path).
+N = 256 or 512, FP32 path), serving (2000 live streams, N in {512, 1024, 2048}, open-loop
+Poisson chunk arrivals through the continuous-batching server; p50/p99 latency).
 
 Printed JSON line:
   value        device-resident throughput (output Gsamples/s, whole job, max over ranks)
@@ -23,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import ctypes
 import hashlib
 import json
 import os
@@ -53,8 +55,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["channels", "single", "mixed", "precision"],
+    ap.add_argument("--workload", choices=["channels", "single", "mixed", "precision", "serving"],
                     default="channels")
+    ap.add_argument("--duration", type=float, default=10.0,
+                    help="serving: seconds of Poisson arrivals")
+    ap.add_argument("--rate", type=float, default=50_000.0, help="serving: chunks/s offered")
+    ap.add_argument("--pool-mb", type=int, default=4096, help="serving: device pool (MiB)")
+    ap.add_argument("--slots", type=int, default=4, help="serving: batch slots")
     ap.add_argument("--channels", type=int, default=None, help="channels / streams per GPU")
     ap.add_argument("--samples", type=int, default=None, help="samples per channel")
     ap.add_argument("--N", type=int, default=256, help="transform size of the precision workload")
@@ -564,6 +571,187 @@ def native_arm(args):
         dist.destroy_process_group()
 
 
+# ---- serving workload --------------------------------------------------------------------------
+
+SERVING = dict(seed=5, nstreams=2000, LV=12, Ns=(512, 1024, 2048), lo=1024, hi=65536,
+               change_frac=0.01)
+
+
+def serving_arm(args):
+    """Open-loop serving: chunks arrive at Poisson times (aggregate --rate chunks/s, stream
+    uniform, length U{1024..65536}, 1% carry a band change) and go through vbw_server_submit /
+    vbw_server_poll as they arrive. Latency = completion time - scheduled arrival. Then a
+    saturation pass submits the same chunks as fast as the queue accepts them (the engine's
+    sustainable throughput). Inputs are pinned host buffers; every sample crosses the host link
+    both ways."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_14116_gb300 import build as vbw_build
+    from paper_2406_14116_gb300 import vbw
+    from paper_2406_14116_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vbw_build.build()
+    c = SERVING
+    V = wl.transition_table(c["seed"], c["LV"])
+    Nsel, Osel, k1 = wl.serving_streams(c["seed"] + rank, c["nstreams"], c["LV"], c["Ns"])
+    t_arr, sid, lens, nbands = wl.serving_arrivals(c["seed"] + rank, c["nstreams"], args.rate,
+                                                   args.duration, c["lo"], c["hi"],
+                                                   c["change_frac"], Nsel, c["LV"])
+    nreq = len(t_arr)
+    plans = [vbw.Plan(N, N // 4, V) for N in c["Ns"]]
+    pidx = {N: i for i, N in enumerate(c["Ns"])}
+    M_of = (Nsel - Nsel // 4).astype(np.int64)
+
+    # pinned host memory: one seeded base signal that every stream reads cyclically from its own
+    # offset, and an output ring that completions free in order
+    base_len = 1 << 22
+    base_t = torch.empty(base_len + c["hi"], dtype=torch.complex64, pin_memory=True)
+    base = base_t.numpy()
+    base[:base_len] = wl.complex_gaussian(c["seed"], 10_000 + rank, base_len)
+    base[base_len:] = base[:c["hi"]]
+    ring_len = 1 << 28
+    ring_t = torch.empty(ring_len, dtype=torch.complex64, pin_memory=True)
+    ring = ring_t.numpy()
+    base_addr, ring_addr = int(base.ctypes.data), int(ring.ctypes.data)
+    soff = (np.arange(c["nstreams"], dtype=np.int64) * 7919 * 97) % base_len
+
+    # per chunk: input address, output count (blocks the chunk completes)
+    pos = np.zeros(c["nstreams"], dtype=np.int64)
+    in_addr = np.empty(nreq, dtype=np.int64)
+    outn = np.empty(nreq, dtype=np.int64)
+    for k in range(nreq):
+        s = sid[k]
+        S = pos[s]
+        in_addr[k] = base_addr + 8 * ((soff[s] + S) % base_len)
+        outn[k] = (S + lens[k]) // M_of[s] * M_of[s] - S // M_of[s] * M_of[s]
+        pos[s] = S + lens[k]
+    L = vbw.lib()
+
+    def ring_place(head, n, tail, outstanding):
+        """Start of n free ring samples at or after head (wrapping to 0), or None if the ring is
+        full. Outputs in flight occupy [tail, head) cyclically."""
+        if not outstanding:
+            return head if head + n <= ring_len else 0
+        if head >= tail:
+            if head + n <= ring_len:
+                return head
+            return 0 if n < tail else None
+        return head if head + n < tail else None
+
+    def run(open_loop: bool, limit: int = nreq):
+        sv = vbw.Server(plans, max_streams=c["nstreams"], pool_bytes=args.pool_mb << 20,
+                        slots=args.slots)
+        for i in range(c["nstreams"]):
+            sv.open_stream(i, pidx[int(Nsel[i])], int(k1[i]))
+        done_t = np.full(nreq, np.nan)
+        out_end = np.zeros(nreq, dtype=np.int64)
+        buf = sv._buf
+        h = sv.handle
+        nd = ctypes.c_int(0)
+        ndp = ctypes.byref(nd)
+        bufp = buf.ctypes.data
+        state = {"tail": 0, "ndone": 0}
+
+        def harvest(block=False):
+            rc = (L.vbw_server_wait if block else L.vbw_server_poll)(h, bufp, len(buf), ndp)
+            if rc != 0:
+                raise vbw.VbwError(rc, vbw.vbw_last_error())
+            n = nd.value
+            if n:
+                tags = buf["tag"][:n]
+                done_t[tags] = buf["t_done"][:n]
+                state["tail"] = int(out_end[tags[-1]])
+                state["ndone"] += n
+            return n
+
+        head = 0
+        clock = L.vbw_server_clock
+        t0 = clock()
+        sched = t0 + t_arr
+        for k in range(limit):
+            if open_loop:
+                while clock() < sched[k]:
+                    harvest()
+            n_out = int(outn[k])
+            # output ring: contiguous space for the chunk's output, freed in completion order
+            if n_out:
+                while True:
+                    at = ring_place(head, n_out, state["tail"], state["ndone"] < k)
+                    if at is not None:
+                        head = at
+                        break
+                    harvest(block=True)
+            rc = L.vbw_server_submit(h, int(sid[k]), int(in_addr[k]), int(lens[k]), int(nbands[k]),
+                                     ring_addr + 8 * head if n_out else 0, n_out, k)
+            if rc != 0:
+                raise vbw.VbwError(rc, vbw.vbw_last_error())
+            out_end[k] = head + n_out
+            head += n_out
+            if not open_loop and (k & 15) == 0:
+                harvest()
+        while state["ndone"] < limit:
+            harvest(block=True)
+        t_end = clock()
+        info = sv.info()
+        sv.close()
+        return sched, done_t, t0, t_end, info
+
+    run(open_loop=False, limit=min(nreq, 4000))     # warm-up: first launches, page-in
+    sampler = ClockSampler(device_uuid(torch, local))
+    sampler.start()
+    sched, done_t, t0, t_end, info = run(open_loop=True)
+    clocks = sampler.stop()
+    lat = (done_t - sched) * 1e3
+    samples = int(lens.sum())
+    span = t_end - t0
+    _, _, s0, s1, info_sat = run(open_loop=False)
+    sat = samples / (s1 - s0) / 1e9
+    vals = torch.tensor([samples / span / 1e9, sat, float(np.percentile(lat, 99))],
+                        dtype=torch.float64, device="cuda")
+    if world > 1:
+        tot = vals.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        vals[0], vals[1] = tot[0], tot[1]
+    value = float(vals[0])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nreq,
+            "warmup": min(nreq, 4000), "ms_per_step": 1e3 * span / nreq, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: {c['nstreams']} streams, N in {list(c['Ns'])}, O = N/4, "
+                                   f"L_V {c['LV']}, Poisson {args.rate:.0f} chunks/s for "
+                                   f"{args.duration:g} s, chunk U{{{c['lo']}..{c['hi']}}}, "
+                                   f"{c['change_frac']:.0%} band changes",
+                       "pool_mib": args.pool_mb, "slots": args.slots,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "host-resident chunks, every sample crosses the host link both ways"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(np.max(lat)),
+                           "from": "scheduled arrival", "to": "outputs on the host (seen by poll)"},
+            "offered_gsamples_s": samples / args.duration / 1e9 * world,
+            "saturation_gsamples_s": float(vals[1]),
+            "batches": info["batches"], "chunks_per_batch": nreq / max(1, info["batches"]),
+            "saturation_batches": info_sat["batches"],
+            "gpu_launches": info["launches"],
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(8 * lens.mean()),
+                    "d2h_bytes_per_step": int(8 * outn.mean()),
+                    "api": "vbw_server_submit / vbw_server_poll, pinned host buffers; a step is one chunk"},
+            "roofline": None, "cpu_baseline": None, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def vbw_tune_shape(tune, torch, N):
     c = tune.load(torch) or {}
     d = c.get("shapes", {}).get(str(N))
@@ -574,6 +762,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "serving":
+        serving_arm(args)
     else:
         native_arm(args)
 
