@@ -2,6 +2,7 @@
 // a GEMM test hook that checks the UMMA operand layout against a host GEMM.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <vector>
 
 #include "ols_tc.cuh"
@@ -16,11 +17,29 @@ static cudaError_t launch_tc_w(const OlsArgs& a, int sms, cudaStream_t st)
     auto kern = ols_tc_kernel<N, PREC, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, G::BYTES);
-    if (e != cudaSuccess) return e;
+    // Resident CTAs per SM, from the SM's shared memory, registers and threads. (The occupancy
+    // calculator reports one CTA per SM for this kernel, while four fit and run concurrently:
+    // measured 43 -> 127 Gsamples/s for BF16 x3 at N = 256.) VBW_TC_CTAS (1..8) overrides it. At
+    // most the TMEM columns of one SM allow: every CTA holds kTcTmemCols.
+    int dev = 0, smem_sm = 0, smem_rsv = 0;
+    cudaFuncAttributes fa;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
+        return e;
+    int per_sm = smem_sm / (int)(G::BYTES + smem_rsv);
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+    if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
+    if (2048 / kTcThreads < per_sm) per_sm = 2048 / kTcThreads;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > 512 / kTcTmemCols) per_sm = 512 / kTcTmemCols;   // TMEM columns of one SM
+    static const int env_ctas = [] {
+        const char* v = getenv("VBW_TC_CTAS");
+        const int c = v ? atoi(v) : 0;
+        return (c >= 1 && c <= 8) ? c : 0;
+    }();
+    if (env_ctas) per_sm = env_ctas;
+    if (per_sm > 512 / kTcTmemCols) per_sm = 512 / kTcTmemCols;
     int64_t grid = (int64_t)per_sm * sms;
     if (grid > a.ntiles) grid = a.ntiles;
     if (grid <= 0) return cudaSuccess;
