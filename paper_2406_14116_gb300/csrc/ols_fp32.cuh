@@ -594,26 +594,11 @@ cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStrea
                              a.ntiles, sms, max_ctas, st, grid_out, &a);
 }
 
-// N = 2048 with overlap N/4 runs on warp pairs (ols_pair.cuh, included by ols_fp32_n2048.cu).
-template <int WARPS, bool BATCH>
-cudaError_t launch_ols_pair_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out);
-
 template <int N>
 cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
     const bool q = (a.overlap == N / 4);
     const bool b = (a.jobs != nullptr);
-    if constexpr (N == 2048) {
-        if (q) {
-            switch (warps) {
-            case 4: return b ? launch_ols_pair_w<4, true>(a, sms, max_ctas, st, grid_out)
-                             : launch_ols_pair_w<4, false>(a, sms, max_ctas, st, grid_out);
-            case 8: return b ? launch_ols_pair_w<8, true>(a, sms, max_ctas, st, grid_out)
-                             : launch_ols_pair_w<8, false>(a, sms, max_ctas, st, grid_out);
-            default: return cudaErrorInvalidValue;
-            }
-        }
-    }
     if (!q) {   // any other even overlap: runtime geometry, 4 warps per CTA
         return b ? launch_ols_fp32_w<N, 4, false, true>(a, sms, max_ctas, st, grid_out)
                  : launch_ols_fp32_w<N, 4, false, false>(a, sms, max_ctas, st, grid_out);

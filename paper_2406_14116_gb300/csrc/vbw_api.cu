@@ -24,7 +24,6 @@ cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, 
                             int* grid_out);
 template <int N>
 cudaError_t launch_export_hr(const float* V, int LV, int k1, float* out, cudaStream_t st);
-cudaError_t launch_export_hr_pair(const float* V, int LV, int k1, float* out, cudaStream_t st);
 cudaError_t launch_ols_mixed(const MixedArgs& a, int maxn, int warps, int sms, int max_ctas,
                              cudaStream_t st, int* grid_out);
 size_t ols_warp_bytes(int N);
@@ -85,27 +84,13 @@ __global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = E + 2;
-    long long j;
-    if (idx < T * row) {
-        // single-warp four-step rows: entry [n2][ka] = W_N^{n2 ka}
-        const int n2 = idx / row, ka = idx % row;
-        if (ka >= E) {
-            tw[idx] = make_float2(0.f, 0.f);
-            return;
-        }
-        j = ((long long)n2 * (long long)ka) % N;
-    } else if (N == 2048 && idx < T * row + 2 * 32 * 34) {
-        // warp-pair tables of N = 2048: the 1024-point four-step rows W_2048^{2 t ka}, then the
-        // split twiddles W_2048^{32 n1 + t}; row t, 32 entries padded to 34
-        const int r = idx - T * row, tab = r / (32 * 34), t = (r % (32 * 34)) / 34, c = r % 34;
-        if (c >= 32) {
-            tw[idx] = make_float2(0.f, 0.f);
-            return;
-        }
-        j = tab == 0 ? (2LL * t * c) % N : 32LL * c + t;
-    } else {
+    if (idx >= T * row) return;
+    const int n2 = idx / row, ka = idx % row;
+    if (ka >= E) {
+        tw[idx] = make_float2(0.f, 0.f);
         return;
     }
+    const long long j = ((long long)n2 * (long long)ka) % N;
     double s, c;
     sincospi(-2.0 * (double)j / (double)N, &s, &c);
     tw[idx] = make_float2((float)c, (float)s);
@@ -222,7 +207,8 @@ static int env_int(const char* name, int dflt)
 }
 
 // Warps per CTA for each N: a tuned value (vbw_tune_set / tune cache), else VBW_WARPS (4 or 8),
-// else 8 (two resident CTAs, 16 warps per SM, for every N with overlap N/4).
+// else the largest CTA whose register footprint keeps 16 resident warps per SM (N <= 1024) or
+// 8 (N = 2048).
 static int warps_for(int N)
 {
     {
@@ -232,7 +218,7 @@ static int warps_for(int N)
     }
     const int w = env_int("VBW_WARPS", 0);
     if (w == 4 || w == 8) return w;
-    return 8;   // N = 2048 runs on warp pairs (overlap N/4) or 4-warp CTAs (other overlaps)
+    return (N <= 1024) ? 8 : 4;
 }
 
 static int ctas_cap_for(int N, int sms)
@@ -286,6 +272,7 @@ int tile_blocks(const vbw_plan_s* p)
 }
 
 // entries of the per-plan twiddle table: T rows of E + 2 (see OlsGeom::TW)
+static int twiddle_entries(int N) { return layout_T(N) * (N / layout_T(N) + 2); }
 
 // ------------------------------------------------------------------------------------------------
 // plans
@@ -918,7 +905,7 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
             mp.N = p->N;
             mp.LV = p->LV;
             mp.tw_off = tw_off;
-            mp.tw_len = twiddle_std_entries(p->N);
+            mp.tw_len = twiddle_entries(p->N);
             tw_off += (mp.tw_len + 1) / 2 * 2;   // keep every table 16-byte aligned
             mixed_warp_bytes = std::max(mixed_warp_bytes, ols_warp_bytes(p->N));
             bt->mixed_groups.push_back((int)bt->groups.size() - 1);
@@ -1240,10 +1227,7 @@ extern "C" vbw_status vbw_debug_export_HR(vbw_plan_t p, int band, float* host_ou
     case 256: e = launch_export_hr<256>(p->d_V, p->LV, band, d, 0); break;
     case 512: e = launch_export_hr<512>(p->d_V, p->LV, band, d, 0); break;
     case 1024: e = launch_export_hr<1024>(p->d_V, p->LV, band, d, 0); break;
-    default:
-        e = p->O == p->N / 4 ? launch_export_hr_pair(p->d_V, p->LV, band, d, 0)
-                             : launch_export_hr<2048>(p->d_V, p->LV, band, d, 0);
-        break;
+    default: e = launch_export_hr<2048>(p->d_V, p->LV, band, d, 0); break;
     }
     if (e == cudaSuccess) e = cudaMemcpy(host_out, d, sizeof(float) * p->N, cudaMemcpyDeviceToHost);
     cudaFree(d);

@@ -94,15 +94,6 @@ inline int layout_T(int N)
     }
 }
 
-// float2 entries of a plan's twiddle array: the single-warp four-step rows (T rows of E + 2), and
-// for N = 2048 the warp-pair tables after them (two 32 x 34 row sets).
-inline int twiddle_std_entries(int N)
-{
-    const int T = layout_T(N);
-    return T ? T * (N / T + 2) : 0;
-}
-inline int twiddle_entries(int N) { return twiddle_std_entries(N) + (N == 2048 ? 2 * 32 * 34 : 0); }
-
 // ---------------------------------------------------------------------------------------------
 // Work descriptors.
 

@@ -32,8 +32,8 @@ namespace {
 
 // Layout of the scratch (bytes). Sized for the largest plan the library accepts (N = 2048,
 // L_V = N/2 - 2), so every valid request fits.
-constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 + 2 x 32 x 34 float2 = 34304 bytes
-constexpr size_t kTwCap = 36864;
+constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 float2 = 16896 bytes
+constexpr size_t kTwCap = 32768;
 constexpr size_t kVOff = kTwOff + kTwCap;    // transition table, float32: at most 4088 bytes
 constexpr size_t kVCap = 8192;
 constexpr size_t kVdOff = kVOff + kVCap;     // transition table as passed (double): <= 8176 bytes
@@ -84,8 +84,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     if (band < 1 || band > N / 2 - LV - 1) return fail_static(VBW_ERR_BAND_RANGE, "band outside [1, N/2-L_V-1]");
     if (nsamples < 0) return fail_static(VBW_ERR_INVALID_ARG, "nsamples < 0");
     const int T = layout_T_of(N), E = N / T;
-    const int tw_entries = vbw::twiddle_entries(N);
-    const size_t tw_bytes = sizeof(float2) * (size_t)tw_entries;
+    const size_t tw_bytes = sizeof(float2) * (size_t)T * (E + 2);
     if (tw_bytes > kTwCap || sizeof(float) * (size_t)LV > kVCap || sizeof(double) * (size_t)LV > kVdCap)
         return fail_static(VBW_ERR_INVALID_ARG, "request exceeds the static scratch (64 KiB)");
     if (nsamples == 0) return vbw::set_error(VBW_OK, "");
@@ -114,6 +113,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     if (cudaMemcpyAsync(Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
         return fail_static(VBW_ERR_CUDA, "table upload failed");
+    const int tw_entries = T * (E + 2);
     vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
     vbw_round_table_kernel<<<(LV + 255) / 256, 256, 0, s>>>(Vd, Vf, LV);
     if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
@@ -133,7 +133,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     a.overlap = overlap;
     a.LV = LV;
     a.status = status;
-    const int warps = 8;
+    const int warps = (N <= 1024) ? 8 : 4;
     int grid = 0;
     cudaError_t e;
     switch (N) {

@@ -101,12 +101,13 @@ def test_empty_and_tiny_signals_in_batch(cuda):
             assert_parity(y.cpu().numpy(), oracle.filter(p.N, p.overlap, V, 9, x))
 
 
-def test_bounded_wait_runs_out_and_reports(cuda):
+@pytest.mark.parametrize("N", [1024, 2048])
+def test_bounded_wait_runs_out_and_reports(cuda, N):
     """A staged copy that never arrives (test hook: the copy is not issued) makes the bounded
     mbarrier wait run out: the kernel sets the status word and the warp returns; the context stays
-    usable and the next launch is correct."""
+    usable and the next launch is correct (N = 1024: 8-warp CTAs, N = 2048: 4-warp CTAs)."""
     torch = cuda
-    N, O = 1024, 256
+    O = N // 4
     M = N - O
     nb = 8000                     # more blocks than resident warps, so warps stage a next block
     V = wl.transition_table(4, 12)

@@ -60,23 +60,19 @@ def test_band_indexing_bit_exact(cuda, N, LV):
     rounded to float32, bit for bit."""
     LV = N // 2 - 2 - 1 if LV == "max" else LV
     V = wl.transition_table(100 + N, LV)
-    # N = 2048 has two kernels with their own gain layouts: the warp pair (overlap N/4) and the
-    # single warp (any other overlap); the export follows the plan's kernel
-    overlaps = [N // 4, 30] if N == 2048 else [N // 4]
+    plan = vbw.Plan(N, N // 4, V)
     bands = range(1, wl.max_band(N, LV) + 1)
     if len(bands) > 300:
         bands = sorted(set(list(range(1, 100)) + list(range(len(bands) - 100, len(bands) + 1)) +
                            list(np.random.default_rng(N).integers(1, len(bands) + 1, 100))))
-    for O in overlaps:
-        plan = vbw.Plan(N, O, V)
-        for k1 in bands:
-            got = vbw.vbw_debug_export_HR(plan.handle, int(k1))
-            want = oracle.HR(N, V, int(k1)).astype(np.float32)
-            np.testing.assert_array_equal(got, want, err_msg=f"N={N} O={O} L_V={LV} k1={k1}")
-        for bad in (0, wl.max_band(N, LV) + 1):
-            with pytest.raises(vbw.VbwError) as e:
-                vbw.vbw_debug_export_HR(plan.handle, bad)
-            assert e.value.code == 2
+    for k1 in bands:
+        got = vbw.vbw_debug_export_HR(plan.handle, int(k1))
+        want = oracle.HR(N, V, int(k1)).astype(np.float32)
+        np.testing.assert_array_equal(got, want, err_msg=f"N={N} L_V={LV} k1={k1}")
+    for bad in (0, wl.max_band(N, LV) + 1):
+        with pytest.raises(vbw.VbwError) as e:
+            vbw.vbw_debug_export_HR(plan.handle, bad)
+        assert e.value.code == 2
 
 
 GEOMS = [(128, 32), (128, 2), (128, 126), (256, 64), (256, 100), (512, 128), (512, 384),

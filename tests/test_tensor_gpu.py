@@ -35,7 +35,7 @@ def test_tcgen05_gemm_layout(cuda, bf16, K, NN):
     np.testing.assert_allclose(D, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
 
 
-PRECS = {vbw.VBW_PREC_BF16_SPLIT: 5e-5, vbw.VBW_PREC_FP16_SCALED: 1e-5,
+PRECS = {vbw.VBW_PREC_BF16_SPLIT: 1e-5, vbw.VBW_PREC_FP16_SCALED: 1e-5,
          vbw.VBW_PREC_BF16_SPLIT3: 1e-5}
 
 
@@ -43,8 +43,7 @@ PRECS = {vbw.VBW_PREC_BF16_SPLIT: 5e-5, vbw.VBW_PREC_FP16_SCALED: 1e-5,
 @pytest.mark.parametrize("prec", list(PRECS))
 def test_tensor_ols_parity(cuda, N, prec):
     """Stream filtering (two calls with the tail carried between them, then a partial block) on
-    the tensor-core kernel vs the oracle. BF16 hi+lo keeps about 16 bits per operand, so its gate
-    is looser; the three-piece BF16 and the scaled FP16 variants meet 1e-5."""
+    the tensor-core kernel vs the oracle, against the 1e-5 RMS gate of the split variants."""
     torch = cuda
     O = N // 4
     M = N - O
