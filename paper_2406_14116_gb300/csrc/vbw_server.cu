@@ -12,9 +12,13 @@
 //      admitted chunks into one job (residual ++ chunks), and launch the batch.
 // The phases of a batch run on three CUDA streams, so batch k+1's copies overlap batch k's
 // kernels:
-//   h2d   chunk copies and one work-list upload                        (copy-in stream)
+//   h2d   one work-list upload, then the chunks into their jobs         (copy-in stream)
 //   comp  residual in, one fused launch per plan, residual out          (compute stream)
 //   d2h   each chunk's completed output blocks to its host buffer       (copy-out stream)
+// Each of the four copy steps is one launch of vbw_copy_kernel over a descriptor list, whatever
+// the number of chunks and streams: the kernel reads and writes pinned host memory directly
+// (NVLink-C2C) and moves residuals inside HBM. Chunks in pageable host memory, which the GPU
+// cannot address, take a cudaMemcpyAsync each instead.
 // Batches depend on each other only through the per-stream device state, which the compute
 // stream orders. Every block runs through the same kernel code whatever else shares its launch,
 // so a stream's output is bit-identical alone and in any mix.
@@ -59,6 +63,8 @@ struct Req {
     const float2* in = nullptr;
     int64_t n = 0;
     float2* out = nullptr;
+    const float2* in_dev = nullptr;   // device address of `in` (pinned memory), or nullptr
+    float2* out_dev = nullptr;        // device address of `out` (pinned memory), or nullptr
     uint64_t tag = 0;
     bool final_flush = false;  // end of stream: the residual becomes a zero-padded last block
     int64_t produced = 0;      // output samples this chunk completes (set when it is launched)
@@ -69,9 +75,9 @@ struct Slot {
     bool busy = false;
     unsigned char* d_region = nullptr;   // chunk inputs and block outputs of one batch
     size_t bytes = 0;
-    unsigned char* h_work = nullptr;     // pinned staging of the work list: jobs | tiles | bands
+    unsigned char* h_work = nullptr;     // pinned staging of the work list (packed per batch)
     unsigned char* d_work = nullptr;
-    size_t tiles_off = 0, bands_off = 0, work_bytes = 0;
+    size_t work_bytes = 0;
     int64_t max_blocks = 0;
     cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr, ev_done = nullptr;
     std::vector<Req> reqs;
@@ -99,6 +105,60 @@ size_t job_bytes(const JobBuild& jb, int M)
     return round256(sizeof(float2) * (size_t)jb.total) + round256(sizeof(float2) * (size_t)(blocks_of(jb, M) * M));
 }
 
+// One contiguous copy of n samples; piece0 = index of its first piece in the launch.
+struct CopyDesc {
+    const float2* src;
+    float2* dst;
+    int64_t n;
+    int64_t piece0;
+};
+constexpr int64_t kCopyPiece = 4096;   // samples per CTA iteration
+constexpr int kMaxReqsPerBatch = 16384;
+
+// Copies every descriptor's samples; a CTA takes one piece of kCopyPiece samples at a time.
+__global__ void __launch_bounds__(256) vbw_copy_kernel(const CopyDesc* d, int nd, int64_t npieces)
+{
+    for (int64_t p = blockIdx.x; p < npieces; p += gridDim.x) {
+        int lo = 0, hi = nd - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].piece0 <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const float2* src = d[lo].src;
+        float2* dst = d[lo].dst;
+        const int64_t s0 = (p - d[lo].piece0) * kCopyPiece;
+        const int64_t s1 = s0 + kCopyPiece < d[lo].n ? s0 + kCopyPiece : d[lo].n;
+#pragma unroll 4
+        for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+// Device address of pinned host memory, or nullptr for pageable memory.
+const void* mapped_host(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
+}
+
+// A descriptor list being filled in the work staging: appends and numbers the pieces.
+struct CopyList {
+    CopyDesc* h = nullptr;
+    int n = 0;
+    int64_t pieces = 0;
+    void add(const float2* src, float2* dst, int64_t cnt)
+    {
+        if (cnt <= 0) return;
+        h[n++] = CopyDesc{src, dst, cnt, pieces};
+        pieces += (cnt + kCopyPiece - 1) / kCopyPiece;
+    }
+};
+
 }  // namespace
 
 struct vbw_server_s {
@@ -111,8 +171,19 @@ struct vbw_server_s {
     unsigned char* d_pool = nullptr;
     float2* d_state = nullptr;           // per-stream tails and residuals
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    int sms = 0;
     int64_t batches = 0, launches = 0, admitted = 0;
 };
+
+// One launch of the copy kernel over a descriptor list already on the device.
+static cudaError_t launch_copies(const vbw_server_s* sv, const CopyDesc* d_desc, const CopyList& l, cudaStream_t st)
+{
+    if (l.n == 0) return cudaSuccess;
+    const int64_t cap = (int64_t)sv->sms * 8;
+    const int grid = (int)(l.pieces < cap ? l.pieces : cap);
+    vbw_copy_kernel<<<grid, 256, 0, st>>>(d_desc, l.n, l.pieces);
+    return cudaGetLastError();
+}
 
 static void server_free(vbw_server_s* sv)
 {
@@ -157,7 +228,10 @@ extern "C" vbw_status vbw_server_create(const vbw_plan_t* plans, int nplans, int
     sv->streams.resize(max_streams);
     sv->slots.resize(slots);
     const size_t stride = round256(sizeof(float2) * (2 * (size_t)maxO + maxM)) / sizeof(float2);
-    bool good = cudaMalloc(&sv->d_pool, slot_bytes * slots) == cudaSuccess &&
+    int dev = 0;
+    bool good = cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                cudaMalloc(&sv->d_pool, slot_bytes * slots) == cudaSuccess &&
                 cudaMalloc(&sv->d_state, sizeof(float2) * stride * max_streams) == cudaSuccess &&
                 cudaStreamCreateWithFlags(&sv->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
                 cudaStreamCreateWithFlags(&sv->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
@@ -176,9 +250,12 @@ extern "C" vbw_status vbw_server_create(const vbw_plan_t* plans, int nplans, int
         sl.d_region = sv->d_pool + slot_bytes * i;
         sl.bytes = slot_bytes;
         sl.max_blocks = max_blocks;
-        sl.tiles_off = round256(sizeof(OlsJob) * (size_t)max_streams);
-        sl.bands_off = sl.tiles_off + round256(sizeof(int2) * (size_t)max_blocks);
-        sl.work_bytes = sl.bands_off + round256(sizeof(int32_t) * (size_t)max_blocks);
+        // packed work list: jobs, tiles, four copy lists (chunks in, residuals in and out, chunks
+        // out), bands; each part 256-byte aligned
+        sl.work_bytes = round256(sizeof(OlsJob) * (size_t)max_streams) + round256(sizeof(int2) * (size_t)max_blocks) +
+                        2 * round256(sizeof(CopyDesc) * (size_t)kMaxReqsPerBatch) +
+                        2 * round256(sizeof(CopyDesc) * (size_t)max_streams) +
+                        round256(sizeof(int32_t) * (size_t)max_blocks);
         good = cudaMallocHost(&sl.h_work, sl.work_bytes) == cudaSuccess &&
                cudaMalloc(&sl.d_work, sl.work_bytes) == cudaSuccess &&
                cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming) == cudaSuccess &&
@@ -255,6 +332,8 @@ extern "C" vbw_status vbw_server_submit(vbw_server_t sv, int stream, const void*
     r.in = static_cast<const float2*>(host_in);
     r.n = n;
     r.out = static_cast<float2*>(host_out);
+    r.in_dev = n > 0 ? static_cast<const float2*>(mapped_host(host_in)) : nullptr;
+    r.out_dev = produce > 0 ? static_cast<float2*>(const_cast<void*>(mapped_host(host_out))) : nullptr;
     r.tag = tag;
     r.t_submit = now_s();
     st.submitted += n;
@@ -276,6 +355,7 @@ extern "C" vbw_status vbw_server_close_stream(vbw_server_t sv, int stream, void*
     Req r;
     r.stream = stream;
     r.out = static_cast<float2*>(host_out);
+    r.out_dev = produce > 0 ? static_cast<float2*>(const_cast<void*>(mapped_host(host_out))) : nullptr;
     r.tag = tag;
     r.final_flush = true;
     r.t_submit = now_s();
@@ -316,6 +396,7 @@ static int launch_batch(vbw_server_s* sv, int si, vbw_status* err)
         const size_t bytes_after = job_bytes(probe, M);
         if (used - bytes_before + bytes_after > sl.bytes) break;
         if (nblocks - nb_before + nb_after > sl.max_blocks) break;
+        if ((int)sl.reqs.size() >= kMaxReqsPerBatch) break;
         used = used - bytes_before + bytes_after;
         nblocks += nb_after - nb_before;
         probe.reqs.push_back(sl.reqs.size());
@@ -340,27 +421,68 @@ static int launch_batch(vbw_server_s* sv, int si, vbw_status* err)
         off += round256(sizeof(float2) * (size_t)(blocks_of(jb, M) * M));
     }
 
-    // ---- copy-in: chunks behind their job's residual
+    // ---- work list, packed: jobs | tiles | chunk-in copies | residual-in | residual-out |
+    //      chunk-out copies | bands (each part 256-byte aligned; sizes counted first)
+    int64_t cnt_jobs = 0, cnt_tiles = 0, cnt_bands = 0;
+    int cnt_cin = 0, cnt_cout = 0, cnt_res = 0;
     for (auto& jb : jobs) {
-        size_t pos = jb.in_off + sizeof(float2) * (size_t)jb.r0;
+        const vbw_plan_s* p = sv->plans[sv->streams[jb.stream].plan];
+        const int64_t nb = blocks_of(jb, p->M);
+        const int B = tile_blocks(p);
+        cnt_bands += nb;
+        cnt_tiles += (nb + B - 1) / B;
+        cnt_jobs += nb > 0;
+        cnt_res += 2;
+        for (size_t ri : jb.reqs) {
+            cnt_cin += sl.reqs[ri].n > 0;
+            cnt_cout += 1;
+        }
+    }
+    size_t woff = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = woff;
+        woff += round256(bytes);
+        return o;
+    };
+    const size_t o_jobs = take(sizeof(OlsJob) * (size_t)cnt_jobs);
+    const size_t o_tiles = take(sizeof(int2) * (size_t)cnt_tiles);
+    const size_t o_cin = take(sizeof(CopyDesc) * (size_t)cnt_cin);
+    const size_t o_rin = take(sizeof(CopyDesc) * (size_t)cnt_res / 2);
+    const size_t o_rout = take(sizeof(CopyDesc) * (size_t)cnt_res / 2);
+    const size_t o_cout = take(sizeof(CopyDesc) * (size_t)cnt_cout);
+    const size_t o_bands = take(sizeof(int32_t) * (size_t)cnt_bands);
+    if (woff > sl.work_bytes) {
+        *err = fail(VBW_ERR_NOMEM, "work list exceeds its staging");
+        return -1;
+    }
+    OlsJob* h_jobs = reinterpret_cast<OlsJob*>(sl.h_work + o_jobs);
+    int2* h_tiles = reinterpret_cast<int2*>(sl.h_work + o_tiles);
+    int32_t* h_bands = reinterpret_cast<int32_t*>(sl.h_work + o_bands);
+    const OlsJob* d_jobs = reinterpret_cast<const OlsJob*>(sl.d_work + o_jobs);
+    const int2* d_tiles = reinterpret_cast<const int2*>(sl.d_work + o_tiles);
+    const int32_t* d_bands = reinterpret_cast<const int32_t*>(sl.d_work + o_bands);
+    CopyList c_in{reinterpret_cast<CopyDesc*>(sl.h_work + o_cin)}, rin{reinterpret_cast<CopyDesc*>(sl.h_work + o_rin)},
+        rout{reinterpret_cast<CopyDesc*>(sl.h_work + o_rout)}, c_out{reinterpret_cast<CopyDesc*>(sl.h_work + o_cout)};
+    std::vector<const Req*> pageable_in;   // chunks the GPU cannot address: one memcpy each
+    std::vector<std::pair<const Req*, size_t>> pageable_out;
+
+    // chunks behind their job's residual; the residual itself comes in on the compute stream
+    for (auto& jb : jobs) {
+        SrvStream& st = sv->streams[jb.stream];
+        float2* jin = reinterpret_cast<float2*>(sl.d_region + jb.in_off);
+        rin.add(st.d_resid, jin, jb.r0);
+        int64_t pos = jb.r0;
         for (size_t ri : jb.reqs) {
             const Req& q = sl.reqs[ri];
-            if (q.n > 0 && cudaMemcpyAsync(sl.d_region + pos, q.in, sizeof(float2) * q.n, cudaMemcpyHostToDevice,
-                                           sv->s_h2d) != cudaSuccess) {
-                *err = fail(VBW_ERR_CUDA, "chunk copy failed");
-                return -1;
+            if (q.n > 0) {
+                if (q.in_dev) c_in.add(q.in_dev, jin + pos, q.n);
+                else pageable_in.push_back(&q);
             }
-            pos += sizeof(float2) * q.n;
+            pos += q.n;
         }
     }
 
-    // ---- work list: jobs grouped by plan, one warp-tile per B blocks, a band per block
-    OlsJob* h_jobs = reinterpret_cast<OlsJob*>(sl.h_work);
-    int2* h_tiles = reinterpret_cast<int2*>(sl.h_work + sl.tiles_off);
-    int32_t* h_bands = reinterpret_cast<int32_t*>(sl.h_work + sl.bands_off);
-    const OlsJob* d_jobs = reinterpret_cast<const OlsJob*>(sl.d_work);
-    const int2* d_tiles = reinterpret_cast<const int2*>(sl.d_work + sl.tiles_off);
-    const int32_t* d_bands = reinterpret_cast<const int32_t*>(sl.d_work + sl.bands_off);
+    // jobs grouped by plan, one warp-tile per B blocks, a band per block
     std::vector<std::pair<int64_t, int64_t>> tile_range(sv->plans.size(), {0, 0});
     int njobs = 0;
     int64_t ntiles = 0, nbands = 0;
@@ -396,38 +518,8 @@ static int launch_batch(vbw_server_s* sv, int si, vbw_status* err)
         }
         tile_range[pl].second = ntiles;
     }
-    if (njobs > 0 &&
-        cudaMemcpyAsync(sl.d_work, sl.h_work, sl.bands_off + sizeof(int32_t) * (size_t)nbands,
-                        cudaMemcpyHostToDevice, sv->s_h2d) != cudaSuccess) {
-        *err = fail(VBW_ERR_CUDA, "work-list upload failed");
-        return -1;
-    }
-    cudaEventRecord(sl.ev_h2d, sv->s_h2d);
 
-    // ---- compute: residual to the front of each job, kernels, new residual back
-    cudaStreamWaitEvent(sv->s_comp, sl.ev_h2d, 0);
-    for (auto& jb : jobs) {
-        const SrvStream& st = sv->streams[jb.stream];
-        if (jb.r0 > 0)
-            cudaMemcpyAsync(sl.d_region + jb.in_off, st.d_resid, sizeof(float2) * (size_t)jb.r0,
-                            cudaMemcpyDeviceToDevice, sv->s_comp);
-    }
-    sl.launches = 0;
-    for (size_t pl = 0; pl < sv->plans.size(); ++pl) {
-        if (tile_range[pl].second <= tile_range[pl].first) continue;
-        OlsArgs a;
-        memset(&a, 0, sizeof(a));
-        a.jobs = d_jobs;
-        a.tiles = d_tiles + tile_range[pl].first;
-        a.ntiles = tile_range[pl].second - tile_range[pl].first;
-        fill_plan_args(a, sv->plans[pl]);
-        const cudaError_t e = launch_plan(sv->plans[pl], a, sv->s_comp);
-        if (e != cudaSuccess) {
-            *err = fail(VBW_ERR_CUDA, "serving launch failed: %s", cudaGetErrorString(e));
-            return -1;
-        }
-        ++sl.launches;
-    }
+    // stream state after this batch: residuals out, block counts, tails flipped
     for (auto& jb : jobs) {
         SrvStream& st = sv->streams[jb.stream];
         const int M = sv->plans[st.plan]->M;
@@ -439,40 +531,82 @@ static int launch_batch(vbw_server_s* sv, int si, vbw_status* err)
             continue;
         }
         const int64_t keep = jb.total - nb * M;
-        if (keep > 0)
-            cudaMemcpyAsync(st.d_resid, sl.d_region + jb.in_off + sizeof(float2) * (size_t)(nb * M),
-                            sizeof(float2) * (size_t)keep, cudaMemcpyDeviceToDevice, sv->s_comp);
+        rout.add(reinterpret_cast<const float2*>(sl.d_region + jb.in_off) + nb * M, st.d_resid, keep);
         st.resid = keep;
         if (nb > 0) st.cur ^= 1;
     }
-    cudaEventRecord(sl.ev_comp, sv->s_comp);
 
-    // ---- copy-out: each chunk's completed blocks
-    cudaStreamWaitEvent(sv->s_d2h, sl.ev_comp, 0);
+    // each chunk's completed blocks
     for (auto& jb : jobs) {
         const int M = sv->plans[sv->streams[jb.stream].plan]->M;
+        const float2* jout = reinterpret_cast<const float2*>(sl.d_region + jb.out_off);
         int64_t cum = jb.r0, emitted = 0;   // job samples through this chunk; output samples handed out
         for (size_t ri : jb.reqs) {
             Req& q = sl.reqs[ri];
             cum += q.n;
             const int64_t upto = q.final_flush ? jb.total : cum / M * M;
             q.produced = upto - emitted;
-            if (q.produced > 0)
-                cudaMemcpyAsync(q.out, sl.d_region + jb.out_off + sizeof(float2) * (size_t)emitted,
-                                sizeof(float2) * (size_t)q.produced, cudaMemcpyDeviceToHost, sv->s_d2h);
+            if (q.produced > 0) {
+                if (q.out_dev) c_out.add(jout + emitted, q.out_dev, q.produced);
+                else pageable_out.push_back({&q, (size_t)emitted});
+            }
             emitted = upto;
         }
     }
-    cudaEventRecord(sl.ev_done, sv->s_d2h);
-    const cudaError_t e = cudaGetLastError();
+
+    // ---- h2d: work list (one copy), chunks in
+    cudaError_t e = cudaMemcpyAsync(sl.d_work, sl.h_work, woff, cudaMemcpyHostToDevice, sv->s_h2d);
+    if (e == cudaSuccess) e = launch_copies(sv, reinterpret_cast<const CopyDesc*>(sl.d_work + o_cin), c_in, sv->s_h2d);
+    for (size_t i = 0; e == cudaSuccess && i < pageable_in.size(); ++i) {
+        const Req& q = *pageable_in[i];
+        const JobBuild& jb = jobs[job_of[q.stream]];
+        int64_t pos = jb.r0;
+        for (size_t ri : jb.reqs) {
+            if (&sl.reqs[ri] == &q) break;
+            pos += sl.reqs[ri].n;
+        }
+        e = cudaMemcpyAsync(sl.d_region + jb.in_off + sizeof(float2) * (size_t)pos, q.in, sizeof(float2) * (size_t)q.n,
+                            cudaMemcpyHostToDevice, sv->s_h2d);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_h2d, sv->s_h2d);
+
+    // ---- compute: residuals in, kernels, residuals out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_comp, sl.ev_h2d, 0);
+    if (e == cudaSuccess) e = launch_copies(sv, reinterpret_cast<const CopyDesc*>(sl.d_work + o_rin), rin, sv->s_comp);
+    sl.launches = 0;
+    for (size_t pl = 0; e == cudaSuccess && pl < sv->plans.size(); ++pl) {
+        if (tile_range[pl].second <= tile_range[pl].first) continue;
+        OlsArgs a;
+        memset(&a, 0, sizeof(a));
+        a.jobs = d_jobs;
+        a.tiles = d_tiles + tile_range[pl].first;
+        a.ntiles = tile_range[pl].second - tile_range[pl].first;
+        fill_plan_args(a, sv->plans[pl]);
+        e = launch_plan(sv->plans[pl], a, sv->s_comp);
+        ++sl.launches;
+    }
+    if (e == cudaSuccess) e = launch_copies(sv, reinterpret_cast<const CopyDesc*>(sl.d_work + o_rout), rout, sv->s_comp);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_comp, sv->s_comp);
+
+    // ---- d2h: chunks out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_d2h, sl.ev_comp, 0);
+    if (e == cudaSuccess) e = launch_copies(sv, reinterpret_cast<const CopyDesc*>(sl.d_work + o_cout), c_out, sv->s_d2h);
+    for (size_t i = 0; e == cudaSuccess && i < pageable_out.size(); ++i) {
+        const Req& q = *pageable_out[i].first;
+        const JobBuild& jb = jobs[job_of[q.stream]];
+        e = cudaMemcpyAsync(q.out, sl.d_region + jb.out_off + sizeof(float2) * pageable_out[i].second,
+                            sizeof(float2) * (size_t)q.produced, cudaMemcpyDeviceToHost, sv->s_d2h);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_done, sv->s_d2h);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = fail(VBW_ERR_CUDA, "batch enqueue failed: %s", cudaGetErrorString(e));
         return -1;
     }
+    sv->launches += sl.launches + (c_in.n > 0) + (rin.n > 0) + (rout.n > 0) + (c_out.n > 0);
     sl.busy = true;
     sv->inflight.push_back(si);
     sv->batches++;
-    sv->launches += sl.launches;
     sv->admitted += (int64_t)sl.reqs.size();
     return (int)sl.reqs.size();
 }

@@ -37,15 +37,18 @@ def _expected_bands(M, band0, chunks):
     return bands[:max(nblocks, 1)], S
 
 
-def _make_streams(seed, specs, torch):
-    """specs: [(plan_index, N, O, band0, [(n, new_band)])] -> input arrays and output buffers."""
+def _make_streams(seed, specs, torch, pageable=()):
+    """specs: [(plan_index, N, O, band0, [(n, new_band)])] -> input arrays and output buffers.
+    Streams listed in `pageable` use pageable numpy memory (copied by the CUDA runtime), the
+    others pinned memory (read and written by the engine's copy kernels)."""
     streams = []
     for i, (pi, N, O, band0, chunks) in enumerate(specs):
         S = sum(n for n, _ in chunks)
         x = wl.complex_gaussian(seed, i, S)
-        xin = _pinned(torch, S)
+        alloc = (lambda n: np.empty(n, dtype=np.complex64)) if i in pageable else (lambda n: _pinned(torch, n))
+        xin = alloc(S)
         xin[:] = x
-        yout = _pinned(torch, S)
+        yout = alloc(S)
         yout[:] = np.nan
         streams.append(dict(plan=pi, N=N, O=O, band0=band0, chunks=chunks, x=xin, y=yout))
     return streams
@@ -136,7 +139,7 @@ def _specs(rng, geo, nstreams, nchunks=6):
 def test_serving_matches_oracle_per_stream(cuda, plans):
     vbw, V, geo, ps = plans
     rng = np.random.default_rng(51)
-    streams = _make_streams(51, _specs(rng, geo, 10), cuda)
+    streams = _make_streams(51, _specs(rng, geo, 10), cuda, pageable={2, 5})
     comp, info = _serve(vbw, ps, streams, pool_bytes=64 << 20, slots=3, order=_order(streams, rng))
     assert info["queued"] == 0 and info["inflight_batches"] == 0
     assert len(comp) == sum(len(s["chunks"]) + 1 for s in streams)
@@ -154,7 +157,7 @@ def test_alone_vs_mix_bitwise(cuda, plans):
     vbw, V, geo, ps = plans
     rng = np.random.default_rng(52)
     specs = _specs(rng, geo, 12, nchunks=8)
-    mixed = _make_streams(52, specs, cuda)
+    mixed = _make_streams(52, specs, cuda, pageable={0, 3, 7, 11})
     _serve(vbw, ps, mixed, pool_bytes=256 << 20, slots=4, order=_order(mixed, rng), poll_every=3)
     for i in (0, 5, 11):
         alone = _make_streams(52, specs, cuda)
