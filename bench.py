@@ -78,6 +78,30 @@ def parse_args():
 KERNEL_SOURCES = ("ols_fp32.cuh", "fft_reg.cuh", "vbw_common.cuh")   # the fused FP32 kernel
 
 
+# ---- cross-rank reductions (replicas: each rank runs its own streams; no data-path collective)
+
+def _group_size() -> int:
+    import torch.distributed as dist
+    return dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+
+
+def rank_reduce(value: float, op: str, device) -> float:
+    """MAX or SUM of a per-rank scalar over the process group (the value itself on one rank)."""
+    if _group_size() == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_gsamples(samples_per_rank: int, steps: int, seconds_per_rank: float, device) -> float:
+    """Whole-job throughput: every rank's samples over the slowest rank's time (weak scaling)."""
+    slowest = rank_reduce(seconds_per_rank, "max", device)
+    return samples_per_rank * _group_size() * steps / slowest / 1e9
+
+
 def source_hash() -> str:
     """Hash of the sources that define the fused FP32 kernel (profiles record it)."""
     h = hashlib.sha256()
@@ -492,12 +516,8 @@ def native_arm(args):
     if bad & set(clocks.get("reasons", [])):
         total_ms, per_ms, clocks = timed()
         remeasured = True
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-
-    value = total * world * args.steps / (total_ms / 1e3) / 1e9
+    value = job_gsamples(total, args.steps, total_ms / 1e3, "cuda")
+    total_ms = rank_reduce(total_ms, "max", "cuda")
     step_ms = float(np.mean(per_ms))
     peak, peak_src = measured_peaks()
     achieved = BYTES_PER_SAMPLE * total / (step_ms / 1e3) / 1e9
@@ -517,11 +537,7 @@ def native_arm(args):
             batch.run_host(views, oviews, stream)
         barrier()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": total * world * k_e2e / dt / 1e9, "unit": UNIT,
+        e2e = {"value": job_gsamples(total, k_e2e, dt, "cuda"), "unit": UNIT,
                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total,
                "steps": k_e2e,
                "api": "vbw_batch_run_host, pinned host buffers (zero copy: the kernels read and "
@@ -712,14 +728,8 @@ def serving_arm(args):
     samples = int(lens.sum())
     span = t_end - t0
     _, _, s0, s1, info_sat = run(open_loop=False)
-    sat = samples / (s1 - s0) / 1e9
-    vals = torch.tensor([samples / span / 1e9, sat, float(np.percentile(lat, 99))],
-                        dtype=torch.float64, device="cuda")
-    if world > 1:
-        tot = vals.clone()
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        vals[0], vals[1] = tot[0], tot[1]
-    value = float(vals[0])
+    value = rank_reduce(samples / span / 1e9, "sum", "cuda")
+    sat = rank_reduce(samples / (s1 - s0) / 1e9, "sum", "cuda")
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nreq,
@@ -736,7 +746,7 @@ def serving_arm(args):
                            "p99": float(np.percentile(lat, 99)), "max": float(np.max(lat)),
                            "from": "scheduled arrival", "to": "outputs on the host (seen by poll)"},
             "offered_gsamples_s": samples / args.duration / 1e9 * world,
-            "saturation_gsamples_s": float(vals[1]),
+            "saturation_gsamples_s": sat,
             "batches": info["batches"], "chunks_per_batch": nreq / max(1, info["batches"]),
             "saturation_batches": info_sat["batches"],
             "gpu_launches": info["launches"],
