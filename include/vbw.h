@@ -183,9 +183,13 @@ vbw_status vbw_tune_set(int N, int warps, int ctas_per_sm);
  * when bit 0 is set. clear != 0 resets the word. */
 vbw_status vbw_plan_status(vbw_plan_t plan, int* flags, int clear);
 
-/* Test hook for the failure-detection path: flags bit 0 makes later launches mark blocks as staged
- * without issuing their copies and shortens the device wait limit to about a millisecond, so the
- * bounded waits run out, set the status word and stop the warp, with no fault. 0 turns it off. */
+/* Test hooks, process-wide; 0 turns them off.
+ *   bit 0: the failure-detection path. Later launches mark blocks as staged without issuing their
+ *          copies and shorten the device wait limit to about a millisecond, so the bounded waits
+ *          run out, set the status word and stop the warp, with no fault.
+ *   bit 1: the full-band identity. Band checks also accept k1 = N/2 + 1, which puts every bin in
+ *          the passband (H_R = 1 in eq. (FS_Hk_real)); the filter then returns its input delayed
+ *          by D = O/2 (eq. (FS_Hk_exp)). */
 vbw_status vbw_debug_set(int flags);
 
 /* Test hook: D (128 x NN) = A (128 x K) B (K x NN) on the tensor cores through the operand

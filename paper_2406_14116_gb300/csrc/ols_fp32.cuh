@@ -31,9 +31,14 @@ struct OlsGeom {
     // row side of each transpose moves two samples per 128-bit access, and offsets consecutive
     // rows by 16 bytes mod 128, so those accesses are conflict-free
     static constexpr int ROW = T + 2;
+    // N = 2048 (two pass-2 DFTs per thread): the transpose runs in two halves of E/2 rows, which
+    // halves the buffer and raises residency from 8 to 12 warps per SM; the next block's N-sample
+    // span would not fit it, so these blocks are not TMA-staged
+    static constexpr bool HALF = (N == 2048);
+    static constexpr bool STAGE = !HALF;
     // per-block transpose buffer; for T = 8 two blocks share a half-warp on the column side, so
     // their buffers are offset by 64 bytes mod 128
-    static constexpr int BLK = E * ROW + ((T == 8) ? 8 : 0);
+    static constexpr int BLK = (HALF ? E / 2 : E) * ROW + ((T == 8) ? 8 : 0);
     // twiddle table row of thread t: W_N^{t ka}, ka = 0..E-1, padded to E + 2
     static constexpr int TWROW = E + 2;
     static constexpr int TW = T * TWROW;
@@ -47,6 +52,7 @@ struct OlsGeom {
     static constexpr size_t GAIN_OFF = BUF_OFF + sizeof(float2) * B * BLK;
     static constexpr size_t WARP_BYTES = (GAIN_OFF + sizeof(float) * B * GT + 15) / 16 * 16;
     static_assert(E * T == N && E % T == 0, "layout must satisfy N = E*T with T | E");
+    static_assert(!HALF || S == 2, "the half transpose assumes two pass-2 DFTs per thread");
     static_assert(BLK % 2 == 0 && T % 2 == 0, "transpose rows must stay 16-byte aligned");
 };
 
@@ -186,19 +192,43 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
         if constexpr (ka != 0) x[ka] = cmul(x[ka], make_float2(w.x, w.y));
         x[ka + 1] = cmul(x[ka + 1], make_float2(w.z, w.w));
     });
-    static_for<0, E>([&](auto ka) { buf[decltype(ka)::value * ROW + t] = x[ka]; });   // F3
-    __syncwarp();
-    static_for<0, S>([&](auto s) {
-        constexpr int SS = decltype(s)::value;
-        const float4* row = reinterpret_cast<const float4*>(buf + (SS * T + t) * ROW);
-        static_for<0, T / 2>([&](auto h) {
-            constexpr int H = decltype(h)::value;
-            const float4 q = row[h];
-            x[SS + S * (2 * H)] = make_float2(q.x, q.y);
-            x[SS + S * (2 * H + 1)] = make_float2(q.z, q.w);
+    if constexpr (!G::HALF) {
+        static_for<0, E>([&](auto ka) { buf[decltype(ka)::value * ROW + t] = x[ka]; });   // F3
+        __syncwarp();
+        static_for<0, S>([&](auto s) {
+            constexpr int SS = decltype(s)::value;
+            const float4* row = reinterpret_cast<const float4*>(buf + (SS * T + t) * ROW);
+            static_for<0, T / 2>([&](auto h) {
+                constexpr int H = decltype(h)::value;
+                const float4 q = row[h];
+                x[SS + S * (2 * H)] = make_float2(q.x, q.y);
+                x[SS + S * (2 * H + 1)] = make_float2(q.z, q.w);
+            });
         });
-    });
-    __syncwarp();
+        __syncwarp();
+    } else {
+        // F3 in two halves: rows ka = SS T + r (r < T) pass through the buffer as rows r; thread
+        // t then reads row t, i.e. ka = SS T + t, the input of its pass-2 DFT number SS
+        float2 half[S][T];
+        static_for<0, S>([&](auto s) {
+            constexpr int SS = decltype(s)::value;
+            static_for<0, T>([&](auto r) { buf[decltype(r)::value * ROW + t] = x[SS * T + decltype(r)::value]; });
+            __syncwarp();
+            const float4* row = reinterpret_cast<const float4*>(buf + t * ROW);
+            static_for<0, T / 2>([&](auto h) {
+                constexpr int H = decltype(h)::value;
+                const float4 q = row[h];
+                half[SS][2 * H] = make_float2(q.x, q.y);
+                half[SS][2 * H + 1] = make_float2(q.z, q.w);
+            });
+            __syncwarp();
+        });
+        static_for<0, S>([&](auto s) {
+            static_for<0, T>([&](auto kp) {
+                x[decltype(s)::value + S * decltype(kp)::value] = half[decltype(s)::value][decltype(kp)::value];
+            });
+        });
+    }
     after_transpose();                  // buf is free from here until the next F3
     static_for<0, S>([&](auto s) {
         constexpr int SS = decltype(s)::value;
@@ -380,6 +410,7 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     for (int pass = 0; pass < 2; ++pass) {
         four_step_dft<N>(x, buf, twrow, t, [&]() {
 #if VBW_TMA_STAGE
+            if constexpr (!G::STAGE) return;
             if (pass != 1 || !has_next || !ctl.bulk) return;
             // the lane group's next block (same plan only): TMA-staged when its span is interior
             OlsJob nj;
@@ -467,7 +498,7 @@ __device__ __forceinline__ void warp_range(int64_t ntiles, int64_t nwarps, int64
 // warp: the overlap samples are L2 hits and the gain table survives until the band changes.
 // QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
 template <int N, int WARPS, bool QOVL, bool BATCH>
-__global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
+__device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
 {
     using G = OlsGeom<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -495,6 +526,19 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
                                    a.overlap, wbase, lane, ws, ctl);
         if (!ok) return;
     }
+}
+
+template <int N, int WARPS, bool QOVL, bool BATCH>
+__global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
+{
+    ols_fp32_body<N, WARPS, QOVL, BATCH>(a);
+}
+
+// N = 2048: registers capped so that three 4-warp CTAs (12 warps) are resident per SM
+template <int WARPS, bool QOVL, bool BATCH>
+__global__ void __launch_bounds__(WARPS * 32, (12 / WARPS) > 0 ? 12 / WARPS : 1) ols_fp32_kernel_2048(const OlsArgs a)
+{
+    ols_fp32_body<2048, WARPS, QOVL, BATCH>(a);
 }
 
 // Mixed-plan persistent kernel: one launch over a tile list whose jobs use different plans with
@@ -590,8 +634,12 @@ cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles,
 template <int N, int WARPS, bool QOVL, bool BATCH>
 cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
-    return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
-                             a.ntiles, sms, max_ctas, st, grid_out, &a);
+    if constexpr (N == 2048)
+        return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
+                                 a.ntiles, sms, max_ctas, st, grid_out, &a);
+    else
+        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
+                                 a.ntiles, sms, max_ctas, st, grid_out, &a);
 }
 
 template <int N>

@@ -163,6 +163,7 @@ static std::mutex g_tune_mu;
 static int g_tune_warps[5] = {0, 0, 0, 0, 0};   // N = 128 << i; 0 = default
 static int g_tune_ctas[5] = {0, 0, 0, 0, 0};    // resident CTAs per SM cap; 0 = occupancy limit
 static int g_wait_limit_debug = 0;               // test hook: skip staging copies, short waits
+static int g_full_band_debug = 0;                // test hook: accept k1 = N/2 + 1 (H_R = 1)
 
 static int n_index(int N)
 {
@@ -184,6 +185,8 @@ static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 vbw_status check_band(const vbw_plan_s* p, int band)
 {
     const int kmax = p->N / 2 - p->LV - 1;
+    // test hook: k1 = N/2 + 1 puts every bin in the passband (H_R = 1, the full-band identity)
+    if (g_full_band_debug && band == p->N / 2 + 1) return VBW_OK;
     if (band < 1 || band > kmax)
         return fail(VBW_ERR_BAND_RANGE, "band k1=%d outside [1, %d] for N=%d, L_V=%d", band, kmax,
                     p->N, p->LV);
@@ -396,6 +399,7 @@ extern "C" vbw_status vbw_tune_set(int N, int warps, int ctas_per_sm)
 extern "C" vbw_status vbw_debug_set(int flags)
 {
     g_wait_limit_debug = flags & 1;
+    g_full_band_debug = (flags >> 1) & 1;
     return ok();
 }
 

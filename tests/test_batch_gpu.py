@@ -101,11 +101,11 @@ def test_empty_and_tiny_signals_in_batch(cuda):
             assert_parity(y.cpu().numpy(), oracle.filter(p.N, p.overlap, V, 9, x))
 
 
-@pytest.mark.parametrize("N", [1024, 2048])
+@pytest.mark.parametrize("N", [512, 1024])
 def test_bounded_wait_runs_out_and_reports(cuda, N):
     """A staged copy that never arrives (test hook: the copy is not issued) makes the bounded
     mbarrier wait run out: the kernel sets the status word and the warp returns; the context stays
-    usable and the next launch is correct (N = 1024: 8-warp CTAs, N = 2048: 4-warp CTAs)."""
+    usable and the next launch is correct. (N = 2048 blocks are not TMA-staged: no wait to run out.)"""
     torch = cuda
     O = N // 4
     M = N - O

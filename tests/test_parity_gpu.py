@@ -274,3 +274,29 @@ def test_channels_workload_reduced(cuda):
     for s, y in zip(w.signals, ys):
         ref = oracle.filter(1024, 256, w.V, s.band, s.x)
         assert_parity(y.cpu().numpy(), ref, what=f"channel {s.stream}")
+
+
+@pytest.mark.parametrize("N,overlap,prec", [(N, N // 4, vbw.VBW_PREC_FP32) for N in ALL_N] +
+                         [(1024, 6, vbw.VBW_PREC_FP32), (2048, 1800, vbw.VBW_PREC_FP32),
+                          (256, 64, vbw.VBW_PREC_BF16_SPLIT), (512, 128, vbw.VBW_PREC_FP16_SCALED)])
+def test_full_band_returns_the_input_delayed(cuda, N, overlap, prec):
+    """With every bin in the passband (H_R = 1, test hook k1 = N/2 + 1) eq. (FS_Hk_exp) leaves
+    only the linear phase, so y(t) = x(t - D), D = O/2, with zeros before the stream (no oracle:
+    the expected output is the shifted input)."""
+    torch = cuda
+    D = overlap // 2
+    V = wl.transition_table(7, 12)
+    M = N - overlap
+    x = wl.complex_gaussian(8, N + overlap, 37 * M + M // 3)
+    vbw.vbw_debug_set(2)
+    try:
+        plan = vbw.Plan(N, overlap, V, precision=prec)
+        y = run_stream(torch, plan, x, N // 2 + 1)
+    finally:
+        vbw.vbw_debug_set(0)
+    want = np.concatenate([np.zeros(D, dtype=np.complex128), x[:len(x) - D]])
+    tol = 2e-6 if prec == vbw.VBW_PREC_FP32 else 1e-5
+    assert_parity(y, want, rms_tol=tol, elem_tol=10 * tol, what=f"N={N} O={overlap} prec={prec}")
+    with pytest.raises(vbw.VbwError) as e:      # outside the test hook the band is rejected
+        vbw.Stream(plan, N // 2 + 1)
+    assert e.value.code == 2
