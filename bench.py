@@ -457,7 +457,12 @@ def native_arm(args):
     torch.cuda.set_stream(side)
     stream = side
     if len(plans) > 1 and not args.no_tune:
-        cfg["batch_mode"] = {k: v for k, v in tune.tune_mixed(torch, batch).items() if k != "table"}
+        tm = tune.tune_mixed(torch, batch)
+        names = {vbw.VBW_BATCH_PER_PLAN: "per_plan", vbw.VBW_BATCH_MIXED: "mixed", vbw.VBW_BATCH_PAIRED: "paired"}
+        cfg["batch_mode"] = {"mode": names.get(tm["mode"], tm["mode"]), "share": tm["share"],
+                             "ms_by_mode": {f"{names.get(r['mode'], r['mode'])}"
+                                            f"{'@' + str(r['share']) if r['mode'] == vbw.VBW_BATCH_MIXED else ''}":
+                                            round(r["ms"], 4) for r in tm["table"]}}
 
     # a CUDA graph of one step (one batch launch, or the mixed launch and its forked branch)
     graph = None
