@@ -458,7 +458,7 @@ def native_arm(args):
     stream = side
     if len(plans) > 1 and not args.no_tune:
         tm = tune.tune_mixed(torch, batch)
-        names = {vbw.VBW_BATCH_PER_PLAN: "per_plan", vbw.VBW_BATCH_MIXED: "mixed", vbw.VBW_BATCH_PAIRED: "paired"}
+        names = {vbw.VBW_BATCH_PER_PLAN: "per_plan", vbw.VBW_BATCH_MIXED: "mixed"}
         cfg["batch_mode"] = {"mode": names.get(tm["mode"], tm["mode"]), "share": tm["share"],
                              "ms_by_mode": {f"{names.get(r['mode'], r['mode'])}"
                                             f"{'@' + str(r['share']) if r['mode'] == vbw.VBW_BATCH_MIXED else ''}":

@@ -167,13 +167,9 @@ vbw_status vbw_batch_launches(vbw_batch_t batch, int* launches);
  *                       (warps switch the transform size per tile), the other plans launched
  *                       beside it on a forked stream; mixed_share is the share of the SMs for the
  *                       mixed launch (0 = in proportion to the transform work);
- *   VBW_BATCH_PAIRED    PER_PLAN, except that the N = 2048 and N = 1024 FP32 plans (overlap N/4)
- *                       run at the same time on a forked stream, each capped so that one CTA of
- *                       each fits on every SM: the N = 2048 kernel holds few warps per SM and
- *                       leaves issue slots that the other kernel's warps fill;
  *   VBW_BATCH_AUTO      MIXED when at least two plans mix, else PER_PLAN (the default).
  * Errors: VBW_ERR_INVALID_ARG. */
-enum { VBW_BATCH_AUTO = 0, VBW_BATCH_PER_PLAN = 1, VBW_BATCH_MIXED = 2, VBW_BATCH_PAIRED = 3 };
+enum { VBW_BATCH_AUTO = 0, VBW_BATCH_PER_PLAN = 1, VBW_BATCH_MIXED = 2 };
 vbw_status vbw_batch_set_mode(vbw_batch_t batch, int mode, double mixed_share);
 
 /* Tuning of the single-plan kernel for transform size N, for every later launch in this process:

@@ -945,7 +945,7 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
 extern "C" vbw_status vbw_batch_set_mode(vbw_batch_t bt, int mode, double mixed_share)
 {
     if (!bt) return fail(VBW_ERR_INVALID_ARG, "batch is NULL");
-    if (mode < VBW_BATCH_AUTO || mode > VBW_BATCH_PAIRED)
+    if (mode < VBW_BATCH_AUTO || mode > VBW_BATCH_MIXED)
         return fail(VBW_ERR_INVALID_ARG, "unknown batch mode %d", mode);
     if (!(mixed_share >= 0.0 && mixed_share < 1.0))
         return fail(VBW_ERR_INVALID_ARG, "mixed_share must be in [0, 1)");
@@ -979,49 +979,6 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st, bool zero_copy 
     const bool use_mixed = bt->mode == VBW_BATCH_MIXED
                                ? !bt->mixed_groups.empty()
                                : (bt->mode == VBW_BATCH_AUTO && bt->mixed_groups.size() >= 2);
-    if (bt->mode == VBW_BATCH_PAIRED) {
-        // the N = 2048 and N = 1024 groups side by side, one CTA of the former per SM and as many
-        // of the latter as fit beside it; then every other group, uncapped, in order
-        int g_big = -1, g_mid = -1;
-        for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
-            const vbw_plan_s* p = bt->groups[gi].plan;
-            if (p->prec != VBW_PREC_FP32 || p->O != p->N / 4) continue;
-            if (p->N == 2048 && g_big < 0) g_big = (int)gi;
-            if (p->N == 1024 && g_mid < 0) g_mid = (int)gi;
-        }
-        if (g_big >= 0 && g_mid >= 0) {
-            const int sms = bt->groups[g_big].plan->sms;
-            int smem_sm = 0, rsv = 0, dev = 0;
-            VBW_CUDA(cudaGetDevice(&dev));
-            VBW_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-            VBW_CUDA(cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-            const size_t big = sizeof(float2) * twiddle_entries(2048) + warps_for(2048) * ols_warp_bytes(2048) + rsv;
-            const size_t mid = sizeof(float2) * twiddle_entries(1024) + warps_for(1024) * ols_warp_bytes(1024) + rsv;
-            const int per_mid = (int)std::max<int64_t>(1, ((int64_t)smem_sm - (int64_t)big) / (int64_t)mid);
-            VBW_CUDA(cudaEventRecord(bt->ev_fork, st));
-            VBW_CUDA(cudaStreamWaitEvent(bt->s_side, bt->ev_fork, 0));
-            const BatchGroup& B = bt->groups[g_big];
-            const BatchGroup& Mg = bt->groups[g_mid];
-            cudaError_t e = launch_group_range(B, 0, B.ntiles, bt->s_side, sms,
-                                               zero_copy ? bt->d_zjobs[g_big] : nullptr, flags);
-            if (e == cudaSuccess)
-                e = launch_group_range(Mg, 0, Mg.ntiles, st, per_mid * sms,
-                                       zero_copy ? bt->d_zjobs[g_mid] : nullptr, flags);
-            if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
-            launches += 2;
-            VBW_CUDA(cudaEventRecord(bt->ev_join, bt->s_side));
-            VBW_CUDA(cudaStreamWaitEvent(st, bt->ev_join, 0));
-            for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
-                if ((int)gi == g_big || (int)gi == g_mid) continue;
-                const BatchGroup& G = bt->groups[gi];
-                e = launch_group_range(G, 0, G.ntiles, st, 0, zero_copy ? bt->d_zjobs[gi] : nullptr, flags);
-                if (e != cudaSuccess) return fail(VBW_ERR_CUDA, "batch launch failed: %s", cudaGetErrorString(e));
-                ++launches;
-            }
-            bt->last_launches = launches;
-            return VBW_OK;
-        }
-    }
     if (!use_mixed) {
         for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
             const BatchGroup& G = bt->groups[gi];

@@ -92,9 +92,6 @@ def tune_mixed(torch, batch, reps: int = 10, shares=(0.0, 0.6, 0.7, 0.8, 0.9)) -
     batch.set_mode(vbw.VBW_BATCH_PER_PLAN)
     table.append({"mode": vbw.VBW_BATCH_PER_PLAN, "share": 0.0,
                   "ms": _time_ms(torch, lambda: batch.run(stream), reps, stream)})
-    batch.set_mode(vbw.VBW_BATCH_PAIRED)
-    table.append({"mode": vbw.VBW_BATCH_PAIRED, "share": 0.0,
-                  "ms": _time_ms(torch, lambda: batch.run(stream), reps, stream)})
     for sh in shares:
         batch.set_mode(vbw.VBW_BATCH_MIXED, sh)
         table.append({"mode": vbw.VBW_BATCH_MIXED, "share": sh,

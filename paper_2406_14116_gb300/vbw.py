@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "VBW_OK", 1: "VBW_ERR_INVALID_ARG", 2: "VBW_ERR_BAND_RANGE", 
                 4: "VBW_ERR_CUDA", 5: "VBW_ERR_TIMEOUT", 6: "VBW_ERR_BUSY", 7: "VBW_ERR_STATE",
                 8: "VBW_ERR_UNSUPPORTED"}
 VBW_PREC_FP32, VBW_PREC_BF16_SPLIT, VBW_PREC_FP16_SCALED, VBW_PREC_BF16_SPLIT3 = 0, 1, 2, 3
-VBW_BATCH_AUTO, VBW_BATCH_PER_PLAN, VBW_BATCH_MIXED, VBW_BATCH_PAIRED = 0, 1, 2, 3
+VBW_BATCH_AUTO, VBW_BATCH_PER_PLAN, VBW_BATCH_MIXED = 0, 1, 2
 
 
 class VbwError(RuntimeError):

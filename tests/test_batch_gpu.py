@@ -25,7 +25,7 @@ def test_mixed_batch_all_modes_match_oracle_and_each_other(cuda):
     torch = cuda
     w, plans, xs, ys, b = mixed_batch(torch)
     outs = {}
-    for mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO, vbw.VBW_BATCH_PAIRED):
+    for mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO):
         for y in ys:
             y.fill_(float("nan"))
         b.set_mode(mode)
@@ -34,12 +34,12 @@ def test_mixed_batch_all_modes_match_oracle_and_each_other(cuda):
         outs[mode] = [y.cpu().numpy() for y in ys]
         if mode == vbw.VBW_BATCH_MIXED:
             assert b.launches == 2      # one mixed launch + the N = 2048 plan beside it
-        if mode in (vbw.VBW_BATCH_PER_PLAN, vbw.VBW_BATCH_PAIRED):
-            assert b.launches == 5      # PAIRED: N = 2048 and 1024 side by side, then the rest
+        if mode == vbw.VBW_BATCH_PER_PLAN:
+            assert b.launches == 5
     for s, y in zip(w.signals, outs[vbw.VBW_BATCH_PER_PLAN]):
         ref = oracle.filter(s.N, s.overlap, w.V, s.band, s.x)
         assert_parity(y, ref, what=f"stream {s.stream} N={s.N} len={len(s.x)}")
-    for mode in (vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO, vbw.VBW_BATCH_PAIRED):
+    for mode in (vbw.VBW_BATCH_MIXED, vbw.VBW_BATCH_AUTO):
         for a, c in zip(outs[vbw.VBW_BATCH_PER_PLAN], outs[mode]):
             np.testing.assert_array_equal(a, c)
 
