@@ -141,6 +141,19 @@ typedef struct {
  * signal pointers; the caller keeps those arrays allocated while the batch is used. */
 vbw_status vbw_batch_create(const vbw_signal* signals, int nsignals, vbw_batch_t* out);
 
+/* Prepares a batch of REAL signals (the paper's setting, Sec. III-D): `in` and `out` are device
+ * float32 arrays of nsamples real samples (4-byte aligned), band_per_block has one entry per real
+ * block of M samples. The filter is real (H(N-k) = conj H(k), eq. (FS_Hk_exp)), so the kernels
+ * take two consecutive real blocks as the real and imaginary parts of one complex block. One
+ * N-point transform pair then yields 2 M real outputs.
+ * Where a band change falls on an odd block, the pair would mix two bands. The signal is then cut
+ * there into pieces, and each later piece reads its O samples of history from the signal itself.
+ * Results equal the complex path on x + 0j (real part).
+ * Errors: VBW_ERR_INVALID_ARG, VBW_ERR_BAND_RANGE, VBW_ERR_UNSUPPORTED (tensor-core plans,
+ * overlap > N/2), VBW_ERR_NOMEM. vbw_batch_run runs it (PER_PLAN launches);
+ * vbw_batch_run_host returns VBW_ERR_UNSUPPORTED for it. */
+vbw_status vbw_batch_create_real(const vbw_signal* signals, int nsignals, vbw_batch_t* out);
+
 /* Runs a prepared batch on cuda_stream: asynchronous, no allocation, no host-device copy, so it
  * can be captured in a CUDA graph. */
 vbw_status vbw_batch_run(vbw_batch_t batch, void* cuda_stream);

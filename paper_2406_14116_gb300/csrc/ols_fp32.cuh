@@ -312,7 +312,12 @@ struct TileCtl {
     bool bulk;            // TMA staging and bulk L2 prefetch allowed (signals in device memory)
 };
 
-template <int N, bool QOVL, class Src>
+// REAL: the job's signal is real (float32). Each lane group then takes the pair of real blocks
+// (2 blk, 2 blk + 1) as one complex block x_{2 blk} + j x_{2 blk + 1}: the filter is real and
+// symmetric (eq. (FS_Hk_exp) is conjugate symmetric), so the real part of the result is the
+// first block's output and the imaginary part the second's. blk counts pairs, and the band is
+// one per pair.
+template <int N, bool QOVL, class Src, bool REAL = false>
 __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_next, int plan,
                                          const float2* tw_plan, const float* V, int LV, int O_rt,
                                          unsigned char* wbase, int lane, WarpState& ws,
@@ -327,6 +332,8 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     const float4* twrow = reinterpret_cast<const float4*>(tw_plan + t * G::TWROW);
     const int O = QOVL ? N / 4 : O_rt;
     const int M = N - O, D = O >> 1;
+    const int64_t P = REAL ? 2 * (int64_t)M : (int64_t)M;   // input samples per lane-group step
+    const int SPAN = REAL ? N + M : N;                      // input samples one step reads
 
     float2 x[E];
     {
@@ -335,7 +342,7 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
         int64_t blk;
         src.template get<B>(tile, bsub, job, blk);
         const int64_t nsamp = job.nsamp;
-        const bool active = blk * M < nsamp;
+        const bool active = blk * P < nsamp;
         const int k1 = src.band(job, blk, active);
         const int key = active ? ((plan << 16) | k1) : ws.table_key;
 
@@ -343,13 +350,24 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
         //      prefetch needs a 16-byte aligned start and a multiple of 16 bytes: a stream whose
         //      base is only 8-byte aligned starts one sample later.
         if (lane == 0 && has_next && ctl.bulk) {
-            int64_t e = (blk + B - 1) * (int64_t)M - O + N;
-            int64_t e2 = e + (int64_t)B * M;
-            if (e2 > nsamp) e2 = nsamp;
-            if (e >= 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) != 0) ++e;
-            const int64_t cnt = (e2 - e) & ~int64_t(1);
-            if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) == 0)
-                prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+            if constexpr (REAL) {
+                const float* in_r = reinterpret_cast<const float*>(job.in);
+                int64_t e = (blk + B - 1) * P - O + SPAN;
+                int64_t e2 = e + (int64_t)B * P;
+                if (e2 > nsamp) e2 = nsamp;
+                while (e >= 0 && e < e2 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) != 0) ++e;
+                const int64_t cnt = (e2 - e) & ~int64_t(3);
+                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) == 0)
+                    prefetch_l2_bulk(in_r + e, (uint32_t)(cnt * sizeof(float)));
+            } else {
+                int64_t e = (blk + B - 1) * (int64_t)M - O + N;
+                int64_t e2 = e + (int64_t)B * M;
+                if (e2 > nsamp) e2 = nsamp;
+                if (e >= 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) != 0) ++e;
+                const int64_t cnt = (e2 - e) & ~int64_t(1);
+                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) == 0)
+                    prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+            }
         }
 
         // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
@@ -362,8 +380,8 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
 
         // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation): from the TMA
         //      staging copy when the previous tile requested it, else from global memory
-        const int64_t s0 = blk * M - O;
-        const bool interior = active && s0 >= 0 && s0 + N <= nsamp;
+        const int64_t s0 = blk * P - O;
+        const bool interior = active && s0 >= 0 && s0 + SPAN <= nsamp;
         uint32_t groups = 0;    // lane groups whose block was staged (warp-uniform)
         {
             const uint32_t leaders = __ballot_sync(0xffffffffu, ws.staged && t == 0);
@@ -385,7 +403,40 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
         }
         ws.phase_mask ^= groups;
         if (__any_sync(0xffffffffu, lost)) return false;
-        if (__all_sync(0xffffffffu, have)) {
+        if constexpr (REAL) {
+            // x(n) = u(s0 + n) + j u(s0 + M + n): the pair's two blocks
+            const float* in_r = reinterpret_cast<const float*>(job.in);
+            const float* tl_r = reinterpret_cast<const float*>(job.tail_in);
+            if (__all_sync(0xffffffffu, have)) {
+                const float* br = reinterpret_cast<const float*>(buf) + t;
+                static_for<0, E>([&](auto n1) {
+                    constexpr int K = decltype(n1)::value * T;
+                    x[n1] = make_float2(br[K], br[M + K]);
+                });
+            } else if (__all_sync(0xffffffffu, interior)) {
+                const float* sp = in_r + s0 + t;
+                static_for<0, E>([&](auto n1) {
+                    constexpr int K = decltype(n1)::value * T;
+                    x[n1] = make_float2(__ldg(sp + K), __ldg(sp + M + K));
+                });
+            } else {
+                auto fr = [&](int64_t si) {
+                    float v = 0.f;
+                    if (active) {
+                        if (si >= 0) {
+                            if (si < nsamp) v = __ldg(in_r + si);
+                        } else if (tl_r) {
+                            v = tl_r[O + si];
+                        }
+                    }
+                    return v;
+                };
+                static_for<0, E>([&](auto n1) {
+                    const int64_t si = s0 + decltype(n1)::value * T + t;
+                    x[n1] = make_float2(fr(si), fr(si + M));
+                });
+            }
+        } else if (__all_sync(0xffffffffu, have)) {
             static_for<0, E>([&](auto n1) { x[n1] = buf[decltype(n1)::value * T + t]; });
         } else if (__all_sync(0xffffffffu, interior)) {
             const float2* sp = job.in + s0 + t;
@@ -416,9 +467,20 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
             OlsJob nj;
             int64_t nb;
             src.template get<B>(tile + 1, bsub, nj, nb);
-            const int64_t ns0 = nb * M - O;
-            if (nj.plan == plan && ns0 >= 0 && ns0 + N <= nj.nsamp &&
-                (reinterpret_cast<uintptr_t>(nj.in + ns0) & 15) == 0) {
+            const int64_t ns0 = nb * P - O;
+            if constexpr (REAL) {
+                const float* nin = reinterpret_cast<const float*>(nj.in) + ns0;
+                const uint32_t bytes = (uint32_t)(SPAN * sizeof(float));
+                if (nj.plan == plan && ns0 >= 0 && ns0 + SPAN <= nj.nsamp && (bytes & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(nin) & 15) == 0) {
+                    if (t == 0 && !(ctl.debug & 1)) {
+                        fence_proxy_async_smem();
+                        tma_load_span(buf, nin, bytes, bar);
+                    }
+                    ws.staged = true;
+                }
+            } else if (nj.plan == plan && ns0 >= 0 && ns0 + N <= nj.nsamp &&
+                       (reinterpret_cast<uintptr_t>(nj.in + ns0) & 15) == 0) {
                 if (t == 0 && !(ctl.debug & 1)) {
                     fence_proxy_async_smem();
                     tma_load_span(buf, nj.in + ns0, (uint32_t)(N * sizeof(float2)), bar);
@@ -446,6 +508,37 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     int64_t blk;
     src.template get<B>(tile, bsub, job, blk);
     const int64_t nsamp = job.nsamp;
+    if constexpr (REAL) {
+        // z(n) = swap(x[n1]): Re z -> block 2 blk, Im z -> block 2 blk + 1, kept D <= n < D + M
+        if (blk * P < nsamp) {
+            float* out_r = reinterpret_cast<float*>(job.out);
+            const int64_t ob = blk * P - D;
+            const bool full = blk * P + P <= nsamp;
+            static_for<0, E>([&](auto n1) {
+                constexpr int N1 = decltype(n1)::value;
+                const int n = N1 * T + t;
+                const bool kept = QOVL ? (N1 >= E / 8 && N1 < 7 * E / 8) : (n >= D && n < D + M);
+                if (kept) {
+                    const int64_t oa = ob + n, obb = ob + M + n;
+                    if (full || oa < nsamp) __stcs(out_r + oa, x[n1].y);
+                    if (full || obb < nsamp) __stcs(out_r + obb, x[n1].x);
+                }
+            });
+            if ((blk + 1) * P >= nsamp && job.tail_out) {
+                const float* in_r = reinterpret_cast<const float*>(job.in);
+                const float* tl_r = reinterpret_cast<const float*>(job.tail_in);
+                float* to_r = reinterpret_cast<float*>(job.tail_out);
+                for (int i = t; i < O; i += T) {
+                    const int64_t si = nsamp - O + i;
+                    float v = 0.f;
+                    if (si >= 0) v = in_r[si];
+                    else if (tl_r) v = tl_r[O + si];
+                    to_r[i] = v;
+                }
+            }
+        }
+        return true;
+    }
     if (blk * M < nsamp) {
         const int64_t obase = blk * M - D;
         if constexpr (QOVL) {
@@ -497,7 +590,7 @@ __device__ __forceinline__ void warp_range(int64_t ntiles, int64_t nwarps, int64
 // Each warp takes one contiguous range of tiles, so consecutive blocks of a stream stay in one
 // warp: the overlap samples are L2 hits and the gain table survives until the band changes.
 // QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
-template <int N, int WARPS, bool QOVL, bool BATCH>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
 __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
 {
     using G = OlsGeom<N>;
@@ -519,7 +612,7 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
     for (int64_t tile = tb; tile < te; ++tile) {
         bool ok;
         if constexpr (BATCH)
-            ok = ols_tile<N, QOVL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0, tw_s, a.V,
+            ok = ols_tile<N, QOVL, JobListSource, REAL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0, tw_s, a.V,
                                    a.LV, a.overlap, wbase, lane, ws, ctl);
         else
             ok = ols_tile<N, QOVL>(SingleJobSource{a}, tile, tile + 1 < te, 0, tw_s, a.V, a.LV,
@@ -528,17 +621,17 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
     }
 }
 
-template <int N, int WARPS, bool QOVL, bool BATCH>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
 __global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
 {
-    ols_fp32_body<N, WARPS, QOVL, BATCH>(a);
+    ols_fp32_body<N, WARPS, QOVL, BATCH, REAL>(a);
 }
 
 // N = 2048: registers capped so that three 4-warp CTAs (12 warps) are resident per SM
-template <int WARPS, bool QOVL, bool BATCH>
+template <int WARPS, bool QOVL, bool BATCH, bool REAL = false>
 __global__ void __launch_bounds__(WARPS * 32, (12 / WARPS) > 0 ? 12 / WARPS : 1) ols_fp32_kernel_2048(const OlsArgs a)
 {
-    ols_fp32_body<2048, WARPS, QOVL, BATCH>(a);
+    ols_fp32_body<2048, WARPS, QOVL, BATCH, REAL>(a);
 }
 
 // Mixed-plan persistent kernel: one launch over a tile list whose jobs use different plans with
@@ -631,14 +724,14 @@ cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles,
     return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(warps * 32), args, smem, st);
 }
 
-template <int N, int WARPS, bool QOVL, bool BATCH>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
 cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
     if constexpr (N == 2048)
-        return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
+        return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH, REAL>, WARPS, ols_smem_bytes<N>(WARPS),
                                  a.ntiles, sms, max_ctas, st, grid_out, &a);
     else
-        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH>, WARPS, ols_smem_bytes<N>(WARPS),
+        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH, REAL>, WARPS, ols_smem_bytes<N>(WARPS),
                                  a.ntiles, sms, max_ctas, st, grid_out, &a);
 }
 
@@ -647,6 +740,15 @@ cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, 
 {
     const bool q = (a.overlap == N / 4);
     const bool b = (a.jobs != nullptr);
+    if (a.flags & kOlsReal) {   // real signals: job lists only
+        if (!b) return cudaErrorInvalidValue;
+        if (!q) return launch_ols_fp32_w<N, 4, false, true, true>(a, sms, max_ctas, st, grid_out);
+        switch (warps) {
+        case 4: return launch_ols_fp32_w<N, 4, true, true, true>(a, sms, max_ctas, st, grid_out);
+        case 8: return launch_ols_fp32_w<N, 8, true, true, true>(a, sms, max_ctas, st, grid_out);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (!q) {   // any other even overlap: runtime geometry, 4 warps per CTA
         return b ? launch_ols_fp32_w<N, 4, false, true>(a, sms, max_ctas, st, grid_out)
                  : launch_ols_fp32_w<N, 4, false, false>(a, sms, max_ctas, st, grid_out);

@@ -134,6 +134,7 @@ struct BatchGroup {
 };
 
 struct vbw_batch_s {
+    bool real = false;              // float32 signals, blocks in pairs (vbw_batch_create_real)
     std::vector<BatchGroup> groups;
     std::vector<vbw_signal> sigs;
     int32_t* d_bands = nullptr;
@@ -804,6 +805,43 @@ static bool mixable(const vbw_plan_s* p)
     return p->prec == VBW_PREC_FP32 && p->O == p->N / 4 && p->N <= 1024;
 }
 
+// Jobs of one real signal. Its blocks go through the kernel in pairs (2q, 2q+1) that share one
+// complex block and therefore one band, so the signal is cut into jobs wherever a band change
+// falls on an odd block: the next job starts at that block and reads its O samples of history
+// from the signal itself (tail_in points O samples before its first input sample).
+struct RealPiece {
+    int64_t first_block, nblocks;   // real blocks [first_block, first_block + nblocks)
+};
+static std::vector<RealPiece> real_pieces(const int32_t* bands, int64_t nb)
+{
+    std::vector<RealPiece> out;
+    int64_t start = 0;
+    while (start < nb) {
+        int64_t end = start;
+        while (end < nb) {
+            if (end + 1 < nb && bands[end] != bands[end + 1]) {
+                end += 1;   // the pair would mix two bands: this piece ends after its first block
+                break;
+            }
+            end += 2;
+        }
+        if (end > nb) end = nb;
+        out.push_back(RealPiece{start, end - start});
+        start = end;
+    }
+    return out;
+}
+
+static vbw_status batch_create_real(const vbw_signal* sig, int n, vbw_batch_t* out);
+
+extern "C" vbw_status vbw_batch_create_real(const vbw_signal* sig, int n, vbw_batch_t* out)
+{
+    if (!out) return fail(VBW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !sig)) return fail(VBW_ERR_INVALID_ARG, "bad signal array");
+    return batch_create_real(sig, n, out);
+}
+
 extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t* out)
 {
     if (!out) return fail(VBW_ERR_INVALID_ARG, "out is NULL");
@@ -942,6 +980,112 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
     return ok();
 }
 
+static vbw_status batch_create_real(const vbw_signal* sig, int n, vbw_batch_t* out)
+{
+    for (int i = 0; i < n; ++i) {
+        const vbw_signal& g = sig[i];
+        if (!g.plan) return fail(VBW_ERR_INVALID_ARG, "signal %d: plan is NULL", i);
+        if (g.plan->prec != VBW_PREC_FP32)
+            return fail(VBW_ERR_UNSUPPORTED, "signal %d: real signals take FP32 plans", i);
+        if (g.plan->O > g.plan->M)
+            return fail(VBW_ERR_UNSUPPORTED, "signal %d: real signals need overlap <= N/2", i);
+        if (g.nsamples < 0) return fail(VBW_ERR_INVALID_ARG, "signal %d: nsamples < 0", i);
+        if (g.nsamples > 0 && (!g.in || !g.out))
+            return fail(VBW_ERR_INVALID_ARG, "signal %d: in/out is NULL", i);
+        if (g.nsamples > 0 && ((((uintptr_t)g.in) & 3) || (((uintptr_t)g.out) & 3)))
+            return fail(VBW_ERR_INVALID_ARG, "signal %d: in/out not 4-byte aligned", i);
+        if (g.nsamples > 0 && ranges_overlap(g.in, g.out, sizeof(float) * (size_t)g.nsamples))
+            return fail(VBW_ERR_INVALID_ARG, "signal %d: in and out overlap", i);
+        const int64_t nb = (g.nsamples + g.plan->M - 1) / g.plan->M;
+        if (nb > INT32_MAX) return fail(VBW_ERR_INVALID_ARG, "signal %d: too many blocks", i);
+        for (int64_t b = 0; b < nb; ++b) {
+            const int k = g.band_per_block ? g.band_per_block[b] : g.band;
+            if (check_band(g.plan, k) != VBW_OK)
+                return fail(VBW_ERR_BAND_RANGE, "signal %d block %lld: band %d out of range", i, (long long)b, k);
+        }
+    }
+    vbw_batch_s* bt = new (std::nothrow) vbw_batch_s();
+    if (!bt) return fail(VBW_ERR_NOMEM, "host allocation failed");
+    memset(&bt->margs, 0, sizeof(bt->margs));
+    bt->real = true;
+    bt->mode = VBW_BATCH_PER_PLAN;
+    bt->sigs.assign(sig, sig + n);
+
+    // pieces of every signal, and one band per block pair of every piece
+    struct Piece {
+        int sig;
+        RealPiece r;
+        int64_t band_off;
+    };
+    std::vector<Piece> pieces;
+    std::vector<int32_t> pair_bands;
+    std::map<vbw_plan_s*, std::vector<int>> by_plan;   // plan -> piece indices
+    for (int i = 0; i < n; ++i) {
+        const vbw_signal& g = sig[i];
+        const int64_t nb = (g.nsamples + g.plan->M - 1) / g.plan->M;
+        std::vector<int32_t> b(nb);
+        for (int64_t k = 0; k < nb; ++k) b[k] = g.band_per_block ? g.band_per_block[k] : g.band;
+        for (const RealPiece& r : real_pieces(b.data(), nb)) {
+            Piece pc{i, r, (int64_t)pair_bands.size()};
+            for (int64_t k = 0; k < r.nblocks; k += 2) pair_bands.push_back(b[r.first_block + k]);
+            by_plan[g.plan].push_back((int)pieces.size());
+            pieces.push_back(pc);
+        }
+    }
+    cudaError_t e = upload(&bt->d_bands, pair_bands);
+    if (e != cudaSuccess) {
+        batch_free(bt);
+        return fail(VBW_ERR_NOMEM, "batch band upload failed: %s", cudaGetErrorString(e));
+    }
+    for (auto& kv : by_plan) {
+        vbw_plan_s* p = kv.first;
+        const int B = tile_blocks(p);
+        std::vector<OlsJob> jobs;
+        std::vector<int2> tiles;
+        BatchGroup gr;
+        gr.plan = p;
+        for (int pi : kv.second) {
+            const Piece& pc = pieces[pi];
+            const vbw_signal& g = sig[pc.sig];
+            const float* in = static_cast<const float*>(g.in) + pc.r.first_block * p->M;
+            float* o = static_cast<float*>(g.out) + pc.r.first_block * p->M;
+            OlsJob j;
+            memset(&j, 0, sizeof(j));
+            j.in = reinterpret_cast<const float2*>(in);
+            j.out = reinterpret_cast<float2*>(o);
+            // history: zeros at the signal start, else the O samples before the piece
+            j.tail_in = pc.r.first_block > 0 ? reinterpret_cast<const float2*>(in - p->O) : nullptr;
+            j.band = bt->d_bands + pc.band_off;
+            j.nsamp = std::min<int64_t>(g.nsamples - pc.r.first_block * p->M, pc.r.nblocks * p->M);
+            j.band0 = pair_bands[(size_t)pc.band_off];
+            j.plan = 0;
+            const int64_t npairs = (pc.r.nblocks + 1) / 2;
+            gr.sig.push_back(pc.sig);
+            gr.tile_off.push_back((int64_t)tiles.size());
+            for (int64_t q = 0; q < npairs; q += B) tiles.push_back(make_int2((int)jobs.size(), (int)q));
+            jobs.push_back(j);
+            gr.cost += (double)npairs * p->N * std::log2((double)p->N);
+        }
+        gr.tile_off.push_back((int64_t)tiles.size());
+        gr.ntiles = (int64_t)tiles.size();
+        cudaError_t e1 = upload(&gr.d_jobs, jobs);
+        cudaError_t e2 = e1 == cudaSuccess ? upload(&gr.d_tiles, tiles) : e1;
+        bt->groups.push_back(gr);
+        if (e2 != cudaSuccess) {
+            batch_free(bt);
+            return fail(VBW_ERR_NOMEM, "batch work-list upload failed: %s", cudaGetErrorString(e2));
+        }
+    }
+    if (cudaStreamCreateWithFlags(&bt->s_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        batch_free(bt);
+        return fail(VBW_ERR_CUDA, "batch stream creation failed");
+    }
+    *out = bt;
+    return ok();
+}
+
 extern "C" vbw_status vbw_batch_set_mode(vbw_batch_t bt, int mode, double mixed_share)
 {
     if (!bt) return fail(VBW_ERR_INVALID_ARG, "batch is NULL");
@@ -975,10 +1119,10 @@ static cudaError_t launch_group_range(const BatchGroup& G, int64_t t0, int64_t t
 static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st, bool zero_copy = false)
 {
     int launches = 0;
-    const int flags = zero_copy ? kOlsNoBulk : 0;
-    const bool use_mixed = bt->mode == VBW_BATCH_MIXED
+    const int flags = (zero_copy ? kOlsNoBulk : 0) | (bt->real ? kOlsReal : 0);
+    const bool use_mixed = !bt->real && bt->mode == VBW_BATCH_MIXED
                                ? !bt->mixed_groups.empty()
-                               : (bt->mode == VBW_BATCH_AUTO && bt->mixed_groups.size() >= 2);
+                               : (!bt->real && bt->mode == VBW_BATCH_AUTO && bt->mixed_groups.size() >= 2);
     if (!use_mixed) {
         for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
             const BatchGroup& G = bt->groups[gi];
@@ -1112,6 +1256,7 @@ extern "C" vbw_status vbw_batch_run_host(vbw_batch_t bt, const void* const* host
 {
     if (!bt || (!bt->sigs.empty() && (!host_in || !host_out)))
         return fail(VBW_ERR_INVALID_ARG, "NULL argument");
+    if (bt->real) return fail(VBW_ERR_UNSUPPORTED, "host buffers are not supported for real batches");
     for (size_t i = 0; i < bt->sigs.size(); ++i)
         if (bt->sigs[i].nsamples > 0 && (!host_in[i] || !host_out[i]))
             return fail(VBW_ERR_INVALID_ARG, "signal %zu: host buffer is NULL", i);

@@ -127,11 +127,13 @@ struct OlsArgs {
     int* status;          // device status word (bit flags, e.g. a bounded wait that gave up) or nullptr
     int64_t wait_limit;   // bound of device-side waits in SM cycles (0 = default, about 2 s)
     int32_t debug;        // test hook, bit 0: skip the staging copies (their waits then run out)
-    int32_t flags;        // kOlsNoBulk: signals live in host memory, use plain loads and stores only
+    int32_t flags;        // kOlsNoBulk: signals live in host memory, use plain loads and stores only;
+                          // kOlsReal: real signals (float32), processed as pairs of blocks
     const unsigned char* tc_tables;   // tensor-core plans: DFT-matrix pieces and twiddles
 };
 
 constexpr int kOlsNoBulk = 1;
+constexpr int kOlsReal = 2;   // the jobs' signals are real float32: blocks go through in pairs
 
 // One plan of a mixed-plan launch (overlap N/4).
 struct MixedPlan {

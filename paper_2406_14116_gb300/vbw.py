@@ -82,6 +82,7 @@ def lib():
         "vbw_stream_save": [p, p, ctypes.POINTER(sz)],
         "vbw_stream_restore": [p, p, sz],
         "vbw_batch_create": [p, i32, pp],
+        "vbw_batch_create_real": [p, i32, pp],
         "vbw_batch_run": [p, p],
         "vbw_batch_run_host": [p, p, p, p],
         "vbw_batch_destroy": [p],
@@ -233,19 +234,31 @@ def vbw_stream_restore(s: int, state: bytes):
     _check(lib().vbw_stream_restore(s, buf, len(state)))
 
 
-def vbw_batch_create(signals) -> int:
-    """signals: sequence of (plan, in, out, nsamples, band, band_per_block or None)."""
+def _dev_ptr_real(x) -> int:
+    if isinstance(x, int):
+        return x
+    import torch
+    if not (hasattr(x, "data_ptr") and x.is_cuda and x.is_contiguous() and x.dtype == torch.float32):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return int(x.data_ptr())
+
+
+def vbw_batch_create(signals, real: bool = False) -> int:
+    """signals: sequence of (plan, in, out, nsamples, band, band_per_block or None); real=True
+    takes float32 signals (vbw_batch_create_real)."""
     arr = (vbw_signal * max(1, len(signals)))()
     keep = []
+    ptr_of = _dev_ptr_real if real else _dev_ptr
     for i, (plan, inp, out, nsamp, band, bpb) in enumerate(signals):
         ptr = None
         if bpb is not None:
             bpb = np.ascontiguousarray(np.asarray(bpb, dtype=np.int32))
             keep.append(bpb)
             ptr = bpb.ctypes.data
-        arr[i] = vbw_signal(plan, _dev_ptr(inp), _dev_ptr(out), int(nsamp), int(band), ptr)
+        arr[i] = vbw_signal(plan, ptr_of(inp), ptr_of(out), int(nsamp), int(band), ptr)
     h = ctypes.c_void_p()
-    _check(lib().vbw_batch_create(arr, len(signals), ctypes.byref(h)))
+    create = lib().vbw_batch_create_real if real else lib().vbw_batch_create
+    _check(create(arr, len(signals), ctypes.byref(h)))
     return h.value
 
 
@@ -450,9 +463,10 @@ class Stream:
 
 
 class Batch:
-    """A prepared batch: signals = [(Plan, in_tensor, out_tensor, band or per-block array)]."""
+    """A prepared batch: signals = [(Plan, in_tensor, out_tensor, band or per-block array)];
+    real=True for float32 signals (pairs of real blocks per complex transform)."""
 
-    def __init__(self, signals):
+    def __init__(self, signals, real: bool = False):
         rows = []
         for plan, inp, out, band in signals:
             n = int(inp.numel())
@@ -461,7 +475,7 @@ class Batch:
             else:
                 b = np.asarray(band, dtype=np.int32)
                 rows.append((plan.handle, inp, out, n, int(b[0]) if len(b) else 1, b))
-        self.handle = vbw_batch_create(rows)
+        self.handle = vbw_batch_create(rows, real)
         self.signals = signals
 
     def run(self, cuda_stream=None):
