@@ -13,8 +13,10 @@
  * OLS steps of Sec. II taken in order.
  *
  * Conventions (readings of the paper, stated once here):
- *   overlap O = N - M = L - 1 (Sec. II, L = N - M + 1); O must be even so that the delay
- *   (L-1)/2 = O/2 is an integer sample count.
+ *   overlap O = N - M = L - 1 (Sec. II, L = N - M + 1); the delay (L-1)/2 = O/2 is a whole
+ *   sample count for even O and a half sample for odd O. The phase of eq. (FS_Hk_exp) takes the
+ *   signed bin index k_s (k for k <= N/2, k - N above), which keeps H conjugate symmetric and the
+ *   impulse response real for odd O too; for even O it equals the unsigned form exactly.
  *   band = k1(b): bins 0..k1-1 are passband; k2 = k1 + L_V - 1 (eq. (k_var), L_V = Delta_N - 1).
  *   Upper-side transition bins use V(N - k - k1) (the real-impulse-response reading of
  *   eq. (FS_Hk_real); it is the one the cosine form of d_{M-1}(q,b) in Sec. III-B implies).
@@ -63,14 +65,15 @@ int vbwo_HR(int N, int LV, const float* V, int k1, double* HR)
  * is exact up to one rounding of 2*pi*j/N. H is written as interleaved (re, im) pairs. */
 int vbwo_H(int N, int O, int LV, const float* V, int k1, double* H)
 {
-    if (O <= 0 || O >= N || (O & 1)) return -1;
+    if (O <= 0 || O >= N) return -1;
     double* HR = (double*)malloc(sizeof(double) * (size_t)N);
     if (!HR) return -1;
     if (vbwo_HR(N, LV, V, k1, HR) != 0) { free(HR); return -1; }
-    const int64_t D = O / 2;
+    /* exp(-j 2 pi k_s (O/2) / N) = exp(-j pi (k_s O mod 2N) / N), reduced exactly in integers */
     for (int k = 0; k < N; ++k) {
-        const int64_t j = ((int64_t)k * D) % N;
-        const double ang = -2.0 * VBWO_PI * (double)j / (double)N;
+        const int64_t ks = k <= N / 2 ? k : (int64_t)k - N;
+        const int64_t j = (((ks * O) % (2 * (int64_t)N)) + 2 * (int64_t)N) % (2 * (int64_t)N);
+        const double ang = -VBWO_PI * (double)j / (double)N;
         H[2 * k] = HR[k] * cos(ang);
         H[2 * k + 1] = HR[k] * sin(ang);
     }
@@ -196,7 +199,7 @@ int vbwo_filter_H(int N, int O, const double* Hri, const float* x, int64_t T, co
 int vbwo_filter(int N, int O, int LV, const float* V, const int32_t* band, const float* x,
                 int64_t T, const float* tail, int64_t b0, int64_t nb, double* y, int nthreads)
 {
-    if (check_geometry(N, O) != 0 || (O & 1) || O == 0 || T < 0 || b0 < 0 || nb < 0) return -1;
+    if (check_geometry(N, O) != 0 || O == 0 || T < 0 || b0 < 0 || nb < 0) return -1;
     const int M = N - O;
     const int64_t nblocks = (T + M - 1) / M;
     if (b0 + nb > nblocks) nb = nblocks > b0 ? nblocks - b0 : 0;

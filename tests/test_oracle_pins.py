@@ -45,6 +45,8 @@ CASES = [
     # N, overlap, LV, k1
     (8, 2, 1, 1), (8, 4, 1, 2), (16, 4, 2, 3), (16, 6, 3, 1), (32, 8, 4, 5),
     (32, 10, 6, 9), (32, 16, 2, 13), (32, 30, 3, 4),
+    # odd overlap: half-sample delay O/2 with the signed-bin phase of eq. (FS_Hk_exp)
+    (16, 5, 2, 3), (32, 9, 4, 5), (32, 15, 3, 7),
 ]
 
 
@@ -74,7 +76,8 @@ def test_brute_force_circular_convolution(N, overlap, LV, k1):
 
 
 @pytest.mark.parametrize("N,overlap,LV,k1", [(64, 16, 5, 7), (128, 32, 15, 41), (128, 32, 15, 48),
-                                             (256, 64, 6, 60), (256, 64, 12, 115)])
+                                             (256, 64, 6, 60), (256, 64, 12, 115),
+                                             (64, 15, 5, 7), (128, 33, 15, 41), (256, 63, 12, 100)])
 def test_H_inverse_dft_is_closed_form(N, overlap, LV, k1):
     """IDFT of the oracle's H(k,b) (numpy's inverse FFT) equals the real cosine sum of
     Sec. III-B: pins the regions, the mirror reading of the upper transition band and the sign of
@@ -87,7 +90,8 @@ def test_H_inverse_dft_is_closed_form(N, overlap, LV, k1):
     np.testing.assert_allclose(h.imag, 0.0, rtol=0, atol=1e-15 * N)
 
 
-@pytest.mark.parametrize("N,overlap,LV", [(32, 8, 3), (64, 16, 6), (128, 32, 15), (256, 64, 12)])
+@pytest.mark.parametrize("N,overlap,LV", [(32, 8, 3), (64, 16, 6), (128, 32, 15), (256, 64, 12),
+                                          (32, 7, 3), (128, 33, 15)])
 def test_last_kept_sample_is_linear_fir(N, overlap, LV):
     """d_{M-1} = IDFT(H) (eq. OLS_dn): the last kept sample of each block equals the linear
     convolution sum_q h(q) x(t - q), t = mM + M - 1, with h the closed form."""
