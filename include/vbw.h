@@ -14,7 +14,10 @@
  *
  * Conventions used by every call:
  *   - Samples are complex64: interleaved (re, im) float32 pairs, 8 bytes per sample.
- *   - N is a power of two in [128, 2048]; overlap O is even with 0 < O < N; M = N - O.
+ *   - N is a power of two in [128, 2048]; overlap 0 < O < N; M = N - O. The delay (L-1)/2 = O/2
+ *     is a whole number of samples for even O. For odd O it is a half sample: the phase of
+ *     eq. (FS_Hk_exp) then uses the signed bin index (k - N above N/2), which keeps the filter
+ *     real. FP32 plans only.
  *   - "band" is k1 of eq. (k_var): bins 0..k1-1 (and their mirrors) are passband, the transition
  *     band is k1..k2 with k2 = k1 + L_V - 1, and 1 <= k1 <= N/2 - L_V - 1 (the paper's bounds
  *     Delta_N/2 <= b_N <= N/2 - Delta_N/2 - 1 with b_N = k1 + Delta_N/2 - 1, L_V = Delta_N - 1).
@@ -68,8 +71,8 @@ enum { VBW_PREC_FP32 = 0, VBW_PREC_BF16_SPLIT = 1, VBW_PREC_FP16_SCALED = 2, VBW
  * V(0..L_V-1) of eq. (FS_Hk_real) (host array, read during the call; any finite values, the
  * paper does not restrict them). The device keeps V rounded to float32 and the FFT twiddles,
  * generated in FP64 on the GPU and rounded once. Needs a current CUDA device.
- * Errors: VBW_ERR_INVALID_ARG (N not a power of two in [128, 2048], overlap odd or outside
- * (0, N), L_V outside [1, N/2 - 2], non-finite V, precision unknown), VBW_ERR_NOMEM, VBW_ERR_CUDA. */
+ * Errors: VBW_ERR_INVALID_ARG (N not a power of two in [128, 2048], overlap outside (0, N),
+ * L_V outside [1, N/2 - 2], non-finite V, precision unknown), VBW_ERR_NOMEM, VBW_ERR_CUDA. */
 vbw_status vbw_plan(int N, int overlap, const double* transition_samples, int L_V, int precision,
                     vbw_plan_t* out);
 vbw_status vbw_plan_destroy(vbw_plan_t plan);

@@ -310,6 +310,7 @@ struct TileCtl {
     long long wait_limit; // bounded-wait limit in SM cycles
     int debug;            // bit 0: mark blocks staged without issuing the copies (test hook)
     bool bulk;            // TMA staging and bulk L2 prefetch allowed (signals in device memory)
+    const float2* half;   // odd overlap: exp(-j pi kk / N), kk = 0..N/2, in shared memory; else null
 };
 
 // REAL: the job's signal is real (float32). Each lane group then takes the pair of real blocks
@@ -331,7 +332,10 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     uint64_t* bar = reinterpret_cast<uint64_t*>(wbase) + bsub;
     const float4* twrow = reinterpret_cast<const float4*>(tw_plan + t * G::TWROW);
     const int O = QOVL ? N / 4 : O_rt;
-    const int M = N - O, D = O >> 1;
+    // D: the store shift, ceil(O/2). For odd O the delay O/2 is a half sample: the whole part
+    // (O - 1)/2 is a shift and the half sample a phase exp(-j pi k_s / N) on every bin, so the kept
+    // outputs start one sample later (z(O + i) of Sec. II steps 4-5 is z'(ceil(O/2) + i))
+    const int M = N - O, D = (O + 1) >> 1;
     const int64_t P = REAL ? 2 * (int64_t)M : (int64_t)M;   // input samples per lane-group step
     const int SPAN = REAL ? N + M : N;                      // input samples one step reads
 
@@ -493,12 +497,29 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
             // swap(g X): H_R(k)/N of eq. (FS_Hk_real) for k = T n1 + t (Sec. II step 2)
             const float* lo = opaque(gtab + t);
             const float* hi = opaque(gtab + (N - t));
-            static_for<0, E>([&](auto n1) {
-                constexpr int N1 = decltype(n1)::value;
-                constexpr int K = N1 * T;
-                const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
-                x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
-            });
+            bool odd = false;
+            if constexpr (!QOVL) odd = ctl.half != nullptr;
+            if (!odd) {
+                static_for<0, E>([&](auto n1) {
+                    constexpr int N1 = decltype(n1)::value;
+                    constexpr int K = N1 * T;
+                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
+                    x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
+                });
+            } else {
+                // the half-sample phase of eq. (FS_Hk_exp) with the signed bin k_s: the table's
+                // exp(-j pi k / N) below N/2, its conjugate at the mirror bin N - k above
+                const float2* plo = ctl.half + t;
+                const float2* phi = ctl.half + (N - t);
+                static_for<0, E>([&](auto n1) {
+                    constexpr int N1 = decltype(n1)::value;
+                    constexpr int K = N1 * T;
+                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
+                    const float2 c = (N1 < E / 2) ? plo[K] : make_float2(phi[-K].x, -phi[-K].y);
+                    const float2 v = cmul(x[n1], c);
+                    x[n1] = make_float2(gk * v.y, gk * v.x);
+                });
+            }
         }
     }
 
@@ -597,16 +618,18 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tw_s = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* wbase = smem_raw + sizeof(float2) * G::TW + (size_t)warp * G::WARP_BYTES;
+    // odd overlap: the plan's half-sample phase table follows its twiddle rows
+    const int ph_len = (!QOVL && (a.overlap & 1)) ? half_phase_entries(N) : 0;
+    unsigned char* wbase = smem_raw + sizeof(float2) * (G::TW + ph_len) + (size_t)warp * G::WARP_BYTES;
 
-    for (int i = threadIdx.x; i < G::TW / 2; i += blockDim.x)
+    for (int i = threadIdx.x; i < (G::TW + ph_len) / 2; i += blockDim.x)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
     if (lane < kMaxGroups) mbar_init(reinterpret_cast<uint64_t*>(wbase) + lane, 1);
     __syncthreads();
 
     WarpState ws{-1, false, 0u};
     const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
-                      (a.flags & kOlsNoBulk) == 0};
+                      (a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
@@ -654,7 +677,7 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
 
     const JobListSource src{a.jobs, a.tiles};
     const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
-                      (a.flags & kOlsNoBulk) == 0};
+                      (a.flags & kOlsNoBulk) == 0, nullptr};
     WarpState ws{-1, false, 0u};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
@@ -727,12 +750,14 @@ cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles,
 template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
 cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
+    const size_t smem = ols_smem_bytes<N>(WARPS) +
+                        ((!QOVL && (a.overlap & 1)) ? sizeof(float2) * half_phase_entries(N) : 0);
     if constexpr (N == 2048)
-        return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH, REAL>, WARPS, ols_smem_bytes<N>(WARPS),
-                                 a.ntiles, sms, max_ctas, st, grid_out, &a);
+        return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH, REAL>, WARPS, smem, a.ntiles, sms,
+                                 max_ctas, st, grid_out, &a);
     else
-        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH, REAL>, WARPS, ols_smem_bytes<N>(WARPS),
-                                 a.ntiles, sms, max_ctas, st, grid_out, &a);
+        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH, REAL>, WARPS, smem, a.ntiles, sms,
+                                 max_ctas, st, grid_out, &a);
 }
 
 template <int N>

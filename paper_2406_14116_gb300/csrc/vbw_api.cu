@@ -96,6 +96,21 @@ __global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E)
     tw[idx] = make_float2((float)c, (float)s);
 }
 
+// Half-sample phase of an odd-overlap plan: ph[kk] = exp(-j pi kk / N), kk = 0..N/2, in FP64
+// rounded once (the exp(-j 2 pi k_s (O/2) / N) of eq. (FS_Hk_exp) past its whole-sample shift).
+__global__ void vbw_halfphase_kernel(float2* ph, int N)
+{
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= half_phase_entries(N)) return;
+    if (kk > N / 2) {
+        ph[kk] = make_float2(0.f, 0.f);
+        return;
+    }
+    double s, c;
+    sincospi(-(double)kk / (double)N, &s, &c);
+    ph[kk] = make_float2((float)c, (float)s);
+}
+
 __global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,8 +303,8 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
     *out = nullptr;
     if (!is_pow2(N) || N < 128 || N > 2048)
         return fail(VBW_ERR_INVALID_ARG, "N=%d: must be a power of two in [128, 2048]", N);
-    if (overlap <= 0 || overlap >= N || (overlap & 1))
-        return fail(VBW_ERR_INVALID_ARG, "overlap=%d: must be even and in (0, N)", overlap);
+    if (overlap <= 0 || overlap >= N)
+        return fail(VBW_ERR_INVALID_ARG, "overlap=%d: must be in (0, N)", overlap);
     if (LV < 1 || LV > N / 2 - 2)
         return fail(VBW_ERR_INVALID_ARG, "L_V=%d: must be in [1, N/2-2]", LV);
     if (!V) return fail(VBW_ERR_INVALID_ARG, "transition_samples is NULL");
@@ -318,7 +333,8 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
             st = fail(VBW_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
             break;
         }
-        if (cudaMalloc(&p->d_tw, sizeof(float2) * twiddle_entries(N)) != cudaSuccess ||
+        const int tw_total = twiddle_entries(N) + ((overlap & 1) ? half_phase_entries(N) : 0);
+        if (cudaMalloc(&p->d_tw, sizeof(float2) * tw_total) != cudaSuccess ||
             cudaMalloc(&p->d_V, sizeof(float) * LV) != cudaSuccess ||
             cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&d_Vd, sizeof(double) * LV) != cudaSuccess) {
@@ -333,6 +349,8 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
         }
         vbw_twiddle_kernel<<<(twiddle_entries(N) + 255) / 256, 256>>>(p->d_tw, N, layout_T(N),
                                                                        N / layout_T(N));
+        if (overlap & 1)
+            vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256>>>(p->d_tw + twiddle_entries(N), N);
         if (precision != VBW_PREC_FP32) {
             if (cudaMalloc(&p->d_tc, tc_table_bytes(N, precision)) != cudaSuccess) {
                 cudaGetLastError();

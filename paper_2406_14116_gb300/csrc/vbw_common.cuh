@@ -81,6 +81,10 @@ template <> struct Layout<512>  { static constexpr int E = 32, T = 16; };
 template <> struct Layout<1024> { static constexpr int E = 32, T = 32; };
 template <> struct Layout<2048> { static constexpr int E = 64, T = 32; };
 
+// Entries (float2) of the half-sample phase table of an odd-overlap plan: exp(-j pi kk / N) for
+// kk = 0..N/2, padded to an even count.
+__host__ __device__ constexpr int half_phase_entries(int N) { return N / 2 + 2; }
+
 // Host mirror of Layout<N>::T (the twiddle table layout depends on it).
 inline int layout_T(int N)
 {

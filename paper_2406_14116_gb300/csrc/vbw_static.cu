@@ -20,6 +20,7 @@
 // Plan-time table kernels of vbw_api.cu.
 __global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E);
 __global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV);
+__global__ void vbw_halfphase_kernel(float2* ph, int N);
 
 namespace vbw {
 template <int N>
@@ -77,14 +78,14 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     using namespace vbw;
     if (N < 128 || N > 2048 || (N & (N - 1)))
         return fail_static(VBW_ERR_INVALID_ARG, "N must be a power of two in [128, 2048]");
-    if (overlap <= 0 || overlap >= N || (overlap & 1))
-        return fail_static(VBW_ERR_INVALID_ARG, "overlap must be even and in (0, N)");
+    if (overlap <= 0 || overlap >= N)
+        return fail_static(VBW_ERR_INVALID_ARG, "overlap must be in (0, N)");
     if (LV < 1 || LV > N / 2 - 2) return fail_static(VBW_ERR_INVALID_ARG, "L_V must be in [1, N/2-2]");
     if (!V) return fail_static(VBW_ERR_INVALID_ARG, "transition_samples is NULL");
     if (band < 1 || band > N / 2 - LV - 1) return fail_static(VBW_ERR_BAND_RANGE, "band outside [1, N/2-L_V-1]");
     if (nsamples < 0) return fail_static(VBW_ERR_INVALID_ARG, "nsamples < 0");
     const int T = layout_T_of(N), E = N / T;
-    const size_t tw_bytes = sizeof(float2) * (size_t)T * (E + 2);
+    const size_t tw_bytes = sizeof(float2) * ((size_t)T * (E + 2) + ((overlap & 1) ? half_phase_entries(N) : 0));
     if (tw_bytes > kTwCap || sizeof(float) * (size_t)LV > kVCap || sizeof(double) * (size_t)LV > kVdCap)
         return fail_static(VBW_ERR_INVALID_ARG, "request exceeds the static scratch (64 KiB)");
     if (nsamples == 0) return vbw::set_error(VBW_OK, "");
@@ -115,6 +116,8 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
         return fail_static(VBW_ERR_CUDA, "table upload failed");
     const int tw_entries = T * (E + 2);
     vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
+    if (overlap & 1)
+        vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256, 0, s>>>(tw + tw_entries, N);
     vbw_round_table_kernel<<<(LV + 255) / 256, 256, 0, s>>>(Vd, Vf, LV);
     if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
 

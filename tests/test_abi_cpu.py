@@ -31,7 +31,7 @@ def test_version_and_empty_error(L):
     (100, 24, 6),      # N not a power of two
     (64, 16, 6),       # N below 128
     (4096, 1024, 12),  # N above 2048
-    (256, 63, 6),      # odd overlap
+    (256, -2, 6),      # negative overlap
     (256, 0, 6),       # no overlap
     (256, 256, 6),     # overlap = N
     (256, 64, 0),      # empty transition table

@@ -300,3 +300,52 @@ def test_full_band_returns_the_input_delayed(cuda, N, overlap, prec):
     with pytest.raises(vbw.VbwError) as e:      # outside the test hook the band is rejected
         vbw.Stream(plan, N // 2 + 1)
     assert e.value.code == 2
+
+
+ODD = [(128, 33), (128, 1), (256, 63), (512, 127), (512, 255), (1024, 255), (1024, 7), (2048, 511),
+       (2048, 1023)]
+
+
+@pytest.mark.parametrize("N,overlap", ODD)
+def test_odd_overlap_half_sample_delay(cuda, N, overlap):
+    """Odd overlap: the delay O/2 is a half sample; the phase of eq. (FS_Hk_exp) takes the signed
+    bin index. Streams in two chunks with a ragged end and band changes, against the oracle."""
+    torch = cuda
+    M = N - overlap
+    V = wl.transition_table(40 + N, 12)
+    plan = vbw.Plan(N, overlap, V)
+    nb = 23
+    x = wl.complex_gaussian(41, N + overlap, nb * M + M // 3 + 1)
+    k1 = int(np.random.default_rng(N + overlap).integers(1, wl.max_band(N, 12) + 1))
+    changes = [(5, max(1, k1 // 2)), (14, wl.max_band(N, 12))]
+    y = run_stream(torch, plan, x, k1, changes=changes, chunks=[9, nb - 9])
+    bands = bands_from_changes((len(x) + M - 1) // M, k1, changes)
+    ref = oracle.filter(N, overlap, V, bands, x)
+    assert_parity(y, ref, what=f"N={N} O={overlap}")
+
+
+@pytest.mark.parametrize("N,overlap", [(256, 63), (1024, 255), (2048, 511)])
+def test_odd_overlap_batch_real_and_no_alloc(cuda, N, overlap):
+    """The same half-sample filter through a batch, the real-signal batch and the no-alloc call."""
+    torch = cuda
+    M = N - overlap
+    V = wl.transition_table(50 + N, 12)
+    plan = vbw.Plan(N, overlap, V)
+    n = 31 * M + 11
+    x = wl.complex_gaussian(51, N, n)
+    nbk = (n + M - 1) // M
+    bands = wl.band_schedule(51, N, nbk, 4, 1, wl.max_band(N, 12))
+    xd = to_dev(torch, x)
+    yd = torch.zeros_like(xd)
+    vbw.Batch([(plan, xd, yd, bands)]).run()
+    xr = np.ascontiguousarray(x.real)
+    xrd = torch.from_numpy(xr).cuda()
+    yrd = torch.zeros_like(xrd)
+    vbw.Batch([(plan, xrd, yrd, bands)], real=True).run()
+    ys = torch.zeros_like(xd)
+    vbw.vbw_filter_static(N, overlap, V, 9, xd, ys, n)
+    torch.cuda.synchronize()
+    assert_parity(yd.cpu().numpy(), oracle.filter(N, overlap, V, bands, x), what="batch")
+    assert_parity(yrd.cpu().numpy(), oracle.filter(N, overlap, V, bands, xr.astype(np.complex64)).real,
+                  what="real batch")
+    assert_parity(ys.cpu().numpy(), oracle.filter(N, overlap, V, 9, x), what="no-alloc")

@@ -27,7 +27,7 @@ def test_no_alloc_rejects_bad_requests_before_touching_the_gpu():
     L = vbw.lib()
     V = np.linspace(0.9, 0.1, 12)
     assert _call(L, 100, 24, V, 5, 0, 0, 10, 0) == 1          # N not a power of two
-    assert _call(L, 256, 63, V, 5, 0, 0, 10, 0) == 1          # odd overlap
+    assert _call(L, 256, 256, V, 5, 0, 0, 10, 0) == 1         # overlap = N
     assert _call(L, 256, 64, V, 0, 0, 0, 10, 0) == 2          # band below range
     assert _call(L, 256, 64, V, 128 - 12, 0, 0, 10, 0) == 2   # band above range
     assert _call(L, 256, 64, V, 5, 0, 0, -1, 0) == 1          # negative length
