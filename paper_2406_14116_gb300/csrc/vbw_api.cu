@@ -1161,7 +1161,7 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st, bool zero_copy 
     if (rest_cost == 0) share = 1.0;
     int mixed_sms = std::max(1, std::min(sms, (int)std::lround(share * sms)));
     if (rest_cost > 0 && mixed_sms == sms) mixed_sms = sms - 1;
-    const int mwarps = 4;
+    const int mwarps = warps_for(1024);   // the largest mixed transform decides the CTA shape
     int mixed_per_sm = 0;
     {
         // CTAs of the mixed kernel that fit on one SM decide how many CTAs its SM share is
