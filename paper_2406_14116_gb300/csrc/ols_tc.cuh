@@ -238,6 +238,28 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
         const int64_t nblocks = (nsamp + M - 1) / M;
         float rs[H2];   // FP16 row scales of the current round's rows
 
+        // ask L2 for the next tile's input span while this tile runs its four rounds
+        if (tid == 0 && tile + 1 < te && (a.flags & kOlsNoBulk) == 0) {
+            OlsJob nj;
+            int64_t nb0;
+            if constexpr (BATCH) {
+                const int2 nd = a.tiles[tile + 1];
+                nj = a.jobs[nd.x];
+                nb0 = nd.y;
+            } else {
+                nj = a.job;
+                nb0 = (tile + 1) * kTcBlocks;
+            }
+            int64_t e = nb0 * M - O;
+            int64_t e2 = (nb0 + kTcBlocks) * M;
+            if (e < 0) e = 0;
+            if (e2 > nj.nsamp) e2 = nj.nsamp;
+            if ((reinterpret_cast<uintptr_t>(nj.in + e) & 15) != 0) ++e;
+            const int64_t cnt = (e2 - e) & ~int64_t(1);
+            if (cnt > 0 && (reinterpret_cast<uintptr_t>(nj.in + e) & 15) == 0)
+                prefetch_l2_bulk(nj.in + e, (uint32_t)(cnt * sizeof(float2)));
+        }
+
         // ---- round 1 input: row tid = (b, n2), x_b(R2 n1 + n2), n1 < R1
         {
             const int b = tid / R2, n2 = tid % R2;
