@@ -115,8 +115,12 @@ struct CopyDesc {
 constexpr int64_t kCopyPiece = 4096;   // samples per CTA iteration
 constexpr int kMaxReqsPerBatch = 16384;
 
-// Copies every descriptor's samples; a CTA takes one piece of kCopyPiece samples at a time.
-__global__ void __launch_bounds__(256) vbw_copy_kernel(const CopyDesc* d, int nd, int64_t npieces)
+// Copies every descriptor's samples; a CTA takes one piece of kCopyPiece samples at a time. Each
+// thread keeps eight loads in flight before it stores them: the sources may be host memory across
+// the CPU-GPU link, where a load takes microseconds.
+constexpr int kCopyThreads = 256, kCopyUnroll = 8;
+__global__ void __launch_bounds__(kCopyThreads) vbw_copy_kernel(const CopyDesc* __restrict__ d, int nd,
+                                                                int64_t npieces)
 {
     for (int64_t p = blockIdx.x; p < npieces; p += gridDim.x) {
         int lo = 0, hi = nd - 1;
@@ -125,12 +129,19 @@ __global__ void __launch_bounds__(256) vbw_copy_kernel(const CopyDesc* d, int nd
             if (d[mid].piece0 <= p) lo = mid;
             else hi = mid - 1;
         }
-        const float2* src = d[lo].src;
-        float2* dst = d[lo].dst;
+        const float2* __restrict__ src = d[lo].src;
+        float2* __restrict__ dst = d[lo].dst;
         const int64_t s0 = (p - d[lo].piece0) * kCopyPiece;
         const int64_t s1 = s0 + kCopyPiece < d[lo].n ? s0 + kCopyPiece : d[lo].n;
-#pragma unroll 4
-        for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) dst[i] = src[i];
+        int64_t i = s0 + threadIdx.x;
+        for (; i + (kCopyUnroll - 1) * kCopyThreads < s1; i += kCopyUnroll * kCopyThreads) {
+            float2 v[kCopyUnroll];
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u) v[u] = __ldcs(src + i + u * kCopyThreads);
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u) __stcs(dst + i + u * kCopyThreads, v[u]);
+        }
+        for (; i < s1; i += kCopyThreads) dst[i] = src[i];
     }
 }
 
@@ -181,7 +192,7 @@ static cudaError_t launch_copies(const vbw_server_s* sv, const CopyDesc* d_desc,
     if (l.n == 0) return cudaSuccess;
     const int64_t cap = (int64_t)sv->sms * 8;
     const int grid = (int)(l.pieces < cap ? l.pieces : cap);
-    vbw_copy_kernel<<<grid, 256, 0, st>>>(d_desc, l.n, l.pieces);
+    vbw_copy_kernel<<<grid, kCopyThreads, 0, st>>>(d_desc, l.n, l.pieces);
     return cudaGetLastError();
 }
 
