@@ -321,6 +321,22 @@ vbw_status vbw_server_open_stream(vbw_server_t server, int stream, int plan, int
 vbw_status vbw_server_submit(vbw_server_t server, int stream, const void* host_in, int64_t n, int new_band,
                              void* host_out, int64_t out_capacity, uint64_t tag);
 
+/* One chunk for vbw_server_submit_many: the arguments of vbw_server_submit. */
+typedef struct {
+    int32_t stream;
+    int32_t new_band;      /* -1: no change */
+    const void* host_in;
+    int64_t n;
+    void* host_out;
+    int64_t out_capacity;
+    uint64_t tag;
+} vbw_request;
+
+/* vbw_server_submit for count chunks in order, in one call (no per-chunk call overhead for the
+ * caller). Stops at the first chunk that fails and returns its status; *submitted is the number
+ * queued before it. */
+vbw_status vbw_server_submit_many(vbw_server_t server, const vbw_request* requests, int count, int* submitted);
+
 /* Queues the end of an open stream. Its completion carries the final partial block (S mod M
  * samples, written to host_out) and final_flush = 1. The stream can be opened again after
  * this call returns. Errors: VBW_ERR_INVALID_ARG (output too small), VBW_ERR_STATE. */

@@ -352,6 +352,20 @@ extern "C" vbw_status vbw_server_submit(vbw_server_t sv, int stream, const void*
     return ok();
 }
 
+extern "C" vbw_status vbw_server_submit_many(vbw_server_t sv, const vbw_request* reqs, int count, int* submitted)
+{
+    if (!sv || !submitted || count < 0 || (count > 0 && !reqs)) return fail(VBW_ERR_INVALID_ARG, "bad argument");
+    *submitted = 0;
+    for (int i = 0; i < count; ++i) {
+        const vbw_request& q = reqs[i];
+        const vbw_status st = vbw_server_submit(sv, q.stream, q.host_in, q.n, q.new_band, q.host_out,
+                                                q.out_capacity, q.tag);
+        if (st != VBW_OK) return st;
+        ++*submitted;
+    }
+    return ok();
+}
+
 extern "C" vbw_status vbw_server_close_stream(vbw_server_t sv, int stream, void* host_out, int64_t out_capacity,
                                               uint64_t tag)
 {

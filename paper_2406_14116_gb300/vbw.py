@@ -37,6 +37,8 @@ class VbwError(RuntimeError):
 # vbw_completion / vbw_server_stats of include/vbw.h as numpy record types
 COMPLETION_DTYPE = np.dtype([("tag", "<u8"), ("stream", "<i4"), ("final_flush", "<i4"),
                              ("produced", "<i8"), ("t_submit", "<f8"), ("t_done", "<f8")])
+REQUEST_DTYPE = np.dtype([("stream", "<i4"), ("new_band", "<i4"), ("host_in", "<u8"), ("n", "<i8"),
+                          ("host_out", "<u8"), ("out_capacity", "<i8"), ("tag", "<u8")])
 SERVER_STATS_FIELDS = ("queued", "inflight_batches", "completions_ready", "batches", "launches",
                        "admitted", "slot_bytes", "slots")
 
@@ -99,6 +101,7 @@ def lib():
         "vbw_server_open_stream": [p, i32, i32, i32],
         "vbw_server_submit": [p, i32, p, i64, i32, p, i64, ctypes.c_uint64],
         "vbw_server_close_stream": [p, i32, p, i64, ctypes.c_uint64],
+        "vbw_server_submit_many": [p, p, i32, p],
         "vbw_server_poll": [p, p, i32, p],
         "vbw_server_wait": [p, p, i32, p],
         "vbw_server_info": [p, p],
@@ -367,6 +370,17 @@ def vbw_server_submit(sv: int, stream: int, host_in, n: int, new_band: int, host
                                    out_capacity, tag))
 
 
+def vbw_server_submit_many(sv: int, requests: np.ndarray) -> int:
+    """requests: REQUEST_DTYPE records (vbw_request). Returns how many were queued; raises on the
+    first failing chunk."""
+    req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+    n = ctypes.c_int(0)
+    code = lib().vbw_server_submit_many(sv, req.ctypes.data, len(req), ctypes.byref(n))
+    if code != VBW_OK:
+        raise VbwError(code, f"{vbw_last_error()} (after {n.value} queued)")
+    return n.value
+
+
 def vbw_server_close_stream(sv: int, stream: int, host_out, out_capacity: int, tag: int):
     _check(lib().vbw_server_close_stream(sv, stream, _hptr(host_out), out_capacity, tag))
 
@@ -522,6 +536,9 @@ class Server:
         if out_capacity is None:
             out_capacity = 0 if host_out is None or isinstance(host_out, int) else len(host_out)
         vbw_server_submit(self.handle, stream, host_in, n, new_band, host_out, out_capacity, tag)
+
+    def submit_many(self, requests: np.ndarray) -> int:
+        return vbw_server_submit_many(self.handle, requests)
 
     def close_stream(self, stream: int, host_out=None, out_capacity: int | None = None, tag: int = 0):
         if out_capacity is None:

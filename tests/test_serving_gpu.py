@@ -288,3 +288,52 @@ def test_serving_workload_sample(cuda):
         assert_parity(ys[i], ref, what=f"serving stream {i} (N={N})")
     for p in ps:
         p.close()
+
+
+def test_submit_many_equals_single_submits(cuda, plans):
+    """vbw_server_submit_many queues the same chunks as one vbw_server_submit per chunk: the outputs
+    are bit-identical; a failing chunk stops the call and reports how many were queued."""
+    vbw, V, geo, ps = plans
+    rng = np.random.default_rng(56)
+    specs = _specs(rng, geo, 6, nchunks=5)
+    one = _make_streams(56, specs, cuda)
+    order = _order(one, rng)
+    _serve(vbw, ps, one, pool_bytes=64 << 20, slots=2, order=order)
+    many = _make_streams(56, specs, cuda)
+    sv = vbw.Server(ps, max_streams=len(many), pool_bytes=64 << 20, slots=2)
+    for i, s in enumerate(many):
+        sv.open_stream(i, s["plan"], s["band0"])
+    nxt, pos, reqs, closes = [0] * len(many), [0] * len(many), [], []
+    for tag, i in enumerate(order):
+        s = many[i]
+        M = s["N"] - s["O"]
+        if nxt[i] < len(s["chunks"]):
+            n, nb = s["chunks"][nxt[i]]
+            S = pos[i]
+            o0 = S // M * M
+            outn = (S + n) // M * M - o0
+            reqs.append((i, nb, s["x"][S:].ctypes.data if n else 0, n,
+                         s["y"][o0:].ctypes.data if outn else 0, outn, tag))
+            pos[i] += n
+        else:
+            closes.append((i, tag))
+        nxt[i] += 1
+    req = np.array(reqs, dtype=vbw.REQUEST_DTYPE)
+    assert sv.submit_many(req) == len(req)
+    for i, tag in closes:
+        s = many[i]
+        M = s["N"] - s["O"]
+        o0 = pos[i] // M * M
+        y = s["y"][o0:]
+        sv.close_stream(i, y if len(y) else None, len(y), tag)
+    sv.drain()
+    for a, b in zip(one, many):
+        np.testing.assert_array_equal(a["y"], b["y"])
+    # a chunk on a stream that is not open stops the call after the good ones
+    bad = np.array([(0, -1, many[0]["x"].ctypes.data, 16, 0, 0, 1), (99, -1, 0, 0, 0, 0, 2)],
+                   dtype=vbw.REQUEST_DTYPE)
+    sv.open_stream(0, many[0]["plan"], many[0]["band0"])
+    with pytest.raises(vbw.VbwError) as e:
+        sv.submit_many(bad)
+    assert "after 1 queued" in str(e.value)
+    sv.close()
