@@ -158,10 +158,9 @@ def test_set_bandwidth_applies_at_next_block(cuda):
     assert_parity(yd.cpu().numpy(), oracle.filter(N, O, V, bands, x), what="set_bandwidth")
 
 
-@pytest.mark.parametrize("N", [128, 1024, 2048])
-def test_chunked_equals_one_shot_bitwise(cuda, N):
+@pytest.mark.parametrize("N,O", [(128, 32), (1024, 256), (2048, 512), (512, 127), (2048, 1023)])
+def test_chunked_equals_one_shot_bitwise(cuda, N, O):
     torch = cuda
-    O = N // 4
     M = N - O
     V = wl.transition_table(5, 12)
     plan = vbw.Plan(N, O, V)
@@ -174,9 +173,9 @@ def test_chunked_equals_one_shot_bitwise(cuda, N):
     np.testing.assert_array_equal(y1, y3)
 
 
-def test_save_restore_bitwise(cuda):
+@pytest.mark.parametrize("N,O", [(1024, 256), (1024, 255)])
+def test_save_restore_bitwise(cuda, N, O):
     torch = cuda
-    N, O = 1024, 256
     M = N - O
     V = wl.transition_table(8, 12)
     plan = vbw.Plan(N, O, V)
@@ -204,9 +203,9 @@ def test_save_restore_bitwise(cuda):
         c.restore(state)
 
 
-def test_filter_host_matches_device(cuda):
+@pytest.mark.parametrize("N,O", [(256, 64), (256, 63)])
+def test_filter_host_matches_device(cuda, N, O):
     torch = cuda
-    N, O = 256, 64
     M = N - O
     V = wl.transition_table(6, 6)
     plan = vbw.Plan(N, O, V)
