@@ -337,3 +337,29 @@ def test_submit_many_equals_single_submits(cuda, plans):
         sv.submit_many(bad)
     assert "after 1 queued" in str(e.value)
     sv.close()
+
+
+def test_serving_tensor_core_plans(cuda):
+    """Streams on tensor-core plans (BF16 split, scaled FP16) go through the same engine: the
+    outputs meet the split variants' 1e-5 gate against the oracle."""
+    from paper_2406_14116_gb300 import vbw
+    V = wl.transition_table(57, LV)
+    ps = [vbw.Plan(256, 64, V, precision=vbw.VBW_PREC_BF16_SPLIT),
+          vbw.Plan(512, 128, V, precision=vbw.VBW_PREC_FP16_SCALED)]
+    geo = [(256, 64), (512, 128)]
+    rng = np.random.default_rng(57)
+    specs = []
+    for i in range(6):
+        pi = i % 2
+        N, O = geo[pi]
+        bmax = wl.max_band(N, LV)
+        specs.append((pi, N, O, int(rng.integers(1, bmax + 1)), _random_chunks(rng, N - O, 6, bmax)))
+    streams = _make_streams(57, specs, cuda)
+    _serve(vbw, ps, streams, pool_bytes=64 << 20, slots=3, order=_order(streams, rng))
+    for i, s in enumerate(streams):
+        M = s["N"] - s["O"]
+        bands, S = _expected_bands(M, s["band0"], s["chunks"])
+        ref = oracle.filter(s["N"], s["O"], V, bands, s["x"])
+        assert_parity(s["y"], ref, rms_tol=1e-5, elem_tol=2e-4, what=f"tensor-core stream {i}")
+    for p in ps:
+        p.close()
