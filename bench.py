@@ -555,6 +555,30 @@ def native_arm(args):
         if not np.array_equal(onp[:n_chk], d_out[:n_chk].cpu().numpy()):
             e2e["mismatch_vs_device_path"] = True
 
+    latency = None
+    if args.workload == "single":
+        # per-call latency of the stream API on this signal: vbw_filter + vbw_flush, synchronized,
+        # host wall time (launch and completion included)
+        s0 = streams[0]
+        M0 = s0.N - s0.overlap
+        plan0 = plans[(s0.N, s0.overlap)]
+        xs, ys = d_in[:s0.nsamples], d_out[:s0.nsamples]
+        nfull = s0.nsamples // M0
+        st_api = vbw.Stream(plan0, int(s0.band[0]), stream)
+        lat = []
+        for k in range(210):
+            st_api.reset(int(s0.band[0]))
+            t0 = time.perf_counter()
+            st_api.filter(xs[:nfull * M0], ys[:nfull * M0], nfull)
+            st_api.flush(xs[nfull * M0:], ys[nfull * M0:], s0.nsamples - nfull * M0)
+            stream.synchronize()
+            if k >= 10:
+                lat.append(time.perf_counter() - t0)
+        lat = np.array(lat) * 1e6
+        latency = {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                   "calls": len(lat), "api": "vbw_filter + vbw_flush on one stream, synchronized"}
+        st_api.close()
+
     cpu = None
     rms = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -587,6 +611,8 @@ def native_arm(args):
             "rms_rel_err_sampled": rms,
             "rms_tol": FP32_RMS_TOL if args.prec == "fp32" else 1e-5,
         }
+        if latency is not None:
+            line["latency_us"] = latency
         if remeasured:
             line["remeasured_after_throttle"] = True
         print(json.dumps(line), flush=True)
