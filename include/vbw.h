@@ -195,14 +195,16 @@ vbw_status vbw_batch_set_mode(vbw_batch_t batch, int mode, double mixed_share);
 vbw_status vbw_tune_set(int N, int warps, int ctas_per_sm);
 
 /* Device status word of a plan's launches (synchronizes the device): bit 0 = a bounded device-side
- * wait gave up (the kernel's warp stopped and its outputs are incomplete). Returns VBW_ERR_TIMEOUT
- * when bit 0 is set. clear != 0 resets the word. */
+ * wait gave up (a tensor-core kernel's CTA waited for its MMAs in vain, stopped, and left its
+ * remaining outputs unwritten). Returns VBW_ERR_TIMEOUT when bit 0 is set. clear != 0 resets the
+ * word. */
 vbw_status vbw_plan_status(vbw_plan_t plan, int* flags, int clear);
 
 /* Test hooks, process-wide; 0 turns them off.
- *   bit 0: the failure-detection path. Later launches mark blocks as staged without issuing their
- *          copies and shorten the device wait limit to about a millisecond, so the bounded waits
- *          run out, set the status word and stop the warp, with no fault.
+ *   bit 0: the failure-detection path. Later launches of tensor-core plans issue no MMAs and
+ *          shorten the device wait limit to about a millisecond, so the bounded waits for the
+ *          accumulators run out, set the status word and stop the CTA, with no fault. (The FP32
+ *          kernels wait on nothing.)
  *   bit 1: the full-band identity. Band checks also accept k1 = N/2 + 1, which puts every bin in
  *          the passband (H_R = 1 in eq. (FS_Hk_real)); the filter then returns its input delayed
  *          by D = O/2 (eq. (FS_Hk_exp)). */

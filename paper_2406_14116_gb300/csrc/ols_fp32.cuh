@@ -32,10 +32,8 @@ struct OlsGeom {
     // rows by 16 bytes mod 128, so those accesses are conflict-free
     static constexpr int ROW = T + 2;
     // N = 2048 (two pass-2 DFTs per thread): the transpose runs in two halves of E/2 rows, which
-    // halves the buffer and raises residency from 8 to 12 warps per SM; the next block's N-sample
-    // span would not fit it, so these blocks are not TMA-staged
+    // halves the buffer and raises residency from 8 to 12 warps per SM
     static constexpr bool HALF = (N == 2048);
-    static constexpr bool STAGE = !HALF;
     // per-block transpose buffer; for T = 8 two blocks share a half-warp on the column side, so
     // their buffers are offset by 64 bytes mod 128
     static constexpr int BLK = (HALF ? E / 2 : E) * ROW + ((T == 8) ? 8 : 0);
@@ -47,8 +45,8 @@ struct OlsGeom {
     static constexpr int GT_MIN = N / 2 + 1;
     static constexpr int GT = (B == 1) ? ((GT_MIN + 3) & ~3)
                                        : GT_MIN + ((T - GT_MIN % 32) % 32 + 32) % 32;
-    // per warp: kMaxGroups mbarriers (fixed place for every N), B transpose buffers, B gain tables
-    static constexpr size_t BUF_OFF = 32;
+    // per warp: B transpose buffers, then B gain tables
+    static constexpr size_t BUF_OFF = 0;
     static constexpr size_t GAIN_OFF = BUF_OFF + sizeof(float2) * B * BLK;
     static constexpr size_t WARP_BYTES = (GAIN_OFF + sizeof(float) * B * GT + 15) / 16 * 16;
     static_assert(E * T == N && E % T == 0, "layout must satisfy N = E*T with T | E");
@@ -89,7 +87,7 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// ---- TMA bulk copy of a block's input span into shared memory, completing on an mbarrier
+// ---- shared-memory addresses and mbarriers (the tensor-core kernel waits on its MMAs with these)
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -101,20 +99,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 }
 
 // generic-proxy accesses to shared memory made before this point are ordered before later
-// async-proxy (TMA) writes
+// async-proxy accesses (the tensor cores' operand reads)
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_span(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%3], %2;\n\t"
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
@@ -141,7 +129,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr long long kWaitLimitCycles = 4000000000LL;   // ~2 s at 2 GHz
-constexpr int kStatusTmaTimeout = 1;
+constexpr int kStatusWaitTimeout = 1;   // status word bit: a bounded device wait gave up
 
 // Gains for the pass-2 layout: g[s][k'] = H_R(k), k = s T + t + E k'. For k' < T/2, k < N/2;
 // otherwise the mirror N - k is used, which makes H_R(N - k) = H_R(k).
@@ -174,21 +162,48 @@ __device__ __forceinline__ P* opaque(P* p)
     return p;
 }
 
+// Shared-memory loads by 32-bit shared address, for tables read inside the tile loop (twiddle
+// rows, gains, half-sample phases). The state space is explicit: a load through a pointer the
+// compiler cannot trace to shared memory would be a generic load on the L1TEX path. The asm is
+// volatile, so each load stays where it is written (its value is not held in registers across
+// the DFT passes).
+__device__ __forceinline__ float lds_f32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float2 lds_f2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float4 lds_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    return v;
+}
+
 // One forward N-point four-step DFT on the register array x (see the top of this file):
 // in:  x[n1] = u(T n1 + t)
 // out: x[n1] = U(T n1 + t)      (with n1 = s + S k', this is X(ka + E k') for ka = s T + t)
 // F1 E-point DFT, F2 twiddle, F3 transpose through buf, F4 S T-point DFTs.
-template <int N, class Hook>
+template <int N>
 __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2* buf,
-                                              const float4* twrow, int t, Hook&& after_transpose)
+                                              const float4* twrow, int t)
 {
     using G = OlsGeom<N>;
     constexpr int E = G::E, T = G::T, S = G::S, ROW = G::ROW;
     fft_reg<E, false>(x);                                                    // F1
-    const float4* tr = opaque(twrow);
+    const uint32_t tr = smem_u32(twrow);
     static_for<0, E / 2>([&](auto kh) {                                      // F2
         constexpr int ka = 2 * decltype(kh)::value;
-        const float4 w = tr[kh];
+        const float4 w = lds_f4(tr + 16 * decltype(kh)::value);
         if constexpr (ka != 0) x[ka] = cmul(x[ka], make_float2(w.x, w.y));
         x[ka + 1] = cmul(x[ka + 1], make_float2(w.z, w.w));
     });
@@ -229,7 +244,6 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
             });
         });
     }
-    after_transpose();                  // buf is free from here until the next F3
     static_for<0, S>([&](auto s) {
         constexpr int SS = decltype(s)::value;
         float2 c[T];
@@ -249,17 +263,12 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
 #ifndef VBW_MIN_WARPS_PER_SM
 #define VBW_MIN_WARPS_PER_SM 0   // 0: no occupancy hint, the compiler chooses the register count
 #endif
-#ifndef VBW_TMA_STAGE
-#define VBW_TMA_STAGE 1          // 1: a warp TMA-stages its next block's span into shared memory
-#endif
 
 #if VBW_MIN_WARPS_PER_SM > 0
 #define VBW_OLS_BOUNDS(W) __launch_bounds__((W) * 32, (VBW_MIN_WARPS_PER_SM / (W)) > 0 ? VBW_MIN_WARPS_PER_SM / (W) : 1)
 #else
 #define VBW_OLS_BOUNDS(W) __launch_bounds__((W) * 32)
 #endif
-
-constexpr int kMaxGroups = 4;   // blocks per warp for the smallest N (T = 8)
 
 // Job sources. The descriptors are re-read through opaque pointers (L1 hits) wherever they are
 // needed, so none of their fields stays live in registers across the DFT passes.
@@ -299,17 +308,11 @@ struct JobListSource {          // device job array + warp-tile list (batches)
 // State a warp carries from one tile to the next.
 struct WarpState {
     int table_key;        // (plan << 16) | k1 of this lane group's gain table; -1 = none
-    bool staged;          // this lane group's next block was requested into its buffer by TMA
-    uint32_t phase_mask;  // bit g: parity of the next completion of mbarrier g (warp-uniform)
 };
 
-// One warp-tile: 32/T blocks of plan `plan`, transform size N. Returns false if the warp has to
-// stop (a staged copy never arrived; the status word says so).
+// Per-launch switches of a warp-tile.
 struct TileCtl {
-    int* status;          // device status word
-    long long wait_limit; // bounded-wait limit in SM cycles
-    int debug;            // bit 0: mark blocks staged without issuing the copies (test hook)
-    bool bulk;            // TMA staging and bulk L2 prefetch allowed (signals in device memory)
+    bool bulk;            // bulk L2 prefetch allowed (signals in device memory)
     const float2* half;   // odd overlap: exp(-j pi kk / N), kk = 0..N/2, in shared memory; else null
 };
 
@@ -318,8 +321,9 @@ struct TileCtl {
 // symmetric (eq. (FS_Hk_exp) is conjugate symmetric), so the real part of the result is the
 // first block's output and the imaginary part the second's. blk counts pairs, and the band is
 // one per pair.
+// One warp-tile: 32/T blocks of plan `plan`, transform size N.
 template <int N, bool QOVL, class Src, bool REAL = false>
-__device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_next, int plan,
+__device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_next, int plan,
                                          const float2* tw_plan, const float* V, int LV, int O_rt,
                                          unsigned char* wbase, int lane, WarpState& ws,
                                          const TileCtl& ctl)
@@ -329,7 +333,6 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
     const int bsub = lane / T, t = lane % T;
     float2* buf = reinterpret_cast<float2*>(wbase + G::BUF_OFF) + bsub * G::BLK;
     float* gtab = reinterpret_cast<float*>(wbase + G::GAIN_OFF) + bsub * G::GT;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase) + bsub;
     const float4* twrow = reinterpret_cast<const float4*>(tw_plan + t * G::TWROW);
     const int O = QOVL ? N / 4 : O_rt;
     // D: the store shift, ceil(O/2). For odd O the delay O/2 is a half sample: the whole part
@@ -382,42 +385,15 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
             __syncwarp();
         }
 
-        // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation): from the TMA
-        //      staging copy when the previous tile requested it, else from global memory
+        // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation), coalesced
+        //      loads from L2 (the span was prefetched by the warp's previous tile)
         const int64_t s0 = blk * P - O;
         const bool interior = active && s0 >= 0 && s0 + SPAN <= nsamp;
-        uint32_t groups = 0;    // lane groups whose block was staged (warp-uniform)
-        {
-            const uint32_t leaders = __ballot_sync(0xffffffffu, ws.staged && t == 0);
-            static_for<0, B>([&](auto g) {
-                if ((leaders >> (decltype(g)::value * T)) & 1u) groups |= 1u << decltype(g)::value;
-            });
-        }
-        bool have = false, lost = false;
-        if (ws.staged) {
-            const uint32_t parity = (ws.phase_mask >> bsub) & 1u;
-            have = mbar_wait_bounded(bar, parity, ctl.wait_limit);
-            if (!have) {
-                // flag it, then wait once more for the copy that may still be in flight
-                if (t == 0 && ctl.status) atomicOr(ctl.status, kStatusTmaTimeout);
-                have = mbar_wait_bounded(bar, parity, ctl.wait_limit);
-                lost = !have;
-            }
-            ws.staged = false;
-        }
-        ws.phase_mask ^= groups;
-        if (__any_sync(0xffffffffu, lost)) return false;
         if constexpr (REAL) {
             // x(n) = u(s0 + n) + j u(s0 + M + n): the pair's two blocks
             const float* in_r = reinterpret_cast<const float*>(job.in);
             const float* tl_r = reinterpret_cast<const float*>(job.tail_in);
-            if (__all_sync(0xffffffffu, have)) {
-                const float* br = reinterpret_cast<const float*>(buf) + t;
-                static_for<0, E>([&](auto n1) {
-                    constexpr int K = decltype(n1)::value * T;
-                    x[n1] = make_float2(br[K], br[M + K]);
-                });
-            } else if (__all_sync(0xffffffffu, interior)) {
+            if (__all_sync(0xffffffffu, interior)) {
                 const float* sp = in_r + s0 + t;
                 static_for<0, E>([&](auto n1) {
                     constexpr int K = decltype(n1)::value * T;
@@ -440,8 +416,6 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
                     x[n1] = make_float2(fr(si), fr(si + M));
                 });
             }
-        } else if (__all_sync(0xffffffffu, have)) {
-            static_for<0, E>([&](auto n1) { x[n1] = buf[decltype(n1)::value * T + t]; });
         } else if (__all_sync(0xffffffffu, interior)) {
             const float2* sp = job.in + s0 + t;
             static_for<0, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
@@ -463,59 +437,38 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
 
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
-        four_step_dft<N>(x, buf, twrow, t, [&]() {
-#if VBW_TMA_STAGE
-            if constexpr (!G::STAGE) return;
-            if (pass != 1 || !has_next || !ctl.bulk) return;
-            // the lane group's next block (same plan only): TMA-staged when its span is interior
-            OlsJob nj;
-            int64_t nb;
-            src.template get<B>(tile + 1, bsub, nj, nb);
-            const int64_t ns0 = nb * P - O;
-            if constexpr (REAL) {
-                const float* nin = reinterpret_cast<const float*>(nj.in) + ns0;
-                const uint32_t bytes = (uint32_t)(SPAN * sizeof(float));
-                if (nj.plan == plan && ns0 >= 0 && ns0 + SPAN <= nj.nsamp && (bytes & 15) == 0 &&
-                    (reinterpret_cast<uintptr_t>(nin) & 15) == 0) {
-                    if (t == 0 && !(ctl.debug & 1)) {
-                        fence_proxy_async_smem();
-                        tma_load_span(buf, nin, bytes, bar);
-                    }
-                    ws.staged = true;
-                }
-            } else if (nj.plan == plan && ns0 >= 0 && ns0 + N <= nj.nsamp &&
-                       (reinterpret_cast<uintptr_t>(nj.in + ns0) & 15) == 0) {
-                if (t == 0 && !(ctl.debug & 1)) {
-                    fence_proxy_async_smem();
-                    tma_load_span(buf, nj.in + ns0, (uint32_t)(N * sizeof(float2)), bar);
-                }
-                ws.staged = true;
-            }
-#endif
-        });
+        four_step_dft<N>(x, buf, twrow, t);
         if (pass == 0) {
             // swap(g X): H_R(k)/N of eq. (FS_Hk_real) for k = T n1 + t (Sec. II step 2)
-            const float* lo = opaque(gtab + t);
-            const float* hi = opaque(gtab + (N - t));
+            const uint32_t lo = smem_u32(gtab + t);
+            const uint32_t hi = smem_u32(gtab + (N - t));
             bool odd = false;
             if constexpr (!QOVL) odd = ctl.half != nullptr;
             if (!odd) {
                 static_for<0, E>([&](auto n1) {
                     constexpr int N1 = decltype(n1)::value;
                     constexpr int K = N1 * T;
-                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
+                    const float gk = (N1 < E / 2) ? lds_f32(lo + 4 * K) : lds_f32(hi - 4 * K);
                     x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
                 });
             } else {
                 // the half-sample phase of eq. (FS_Hk_exp) with the signed bin k_s: the table's
                 // exp(-j pi k / N) below N/2, its conjugate at the mirror bin N - k above
-                const float2* plo = ctl.half + t;
-                const float2* phi = ctl.half + (N - t);
+                const uint32_t plo = smem_u32(ctl.half + t);
+                const uint32_t phi = smem_u32(ctl.half + (N - t));
                 static_for<0, E>([&](auto n1) {
                     constexpr int N1 = decltype(n1)::value;
                     constexpr int K = N1 * T;
-                    const float gk = (N1 < E / 2) ? lo[K] : hi[-K];
-                    const float2 c = (N1 < E / 2) ? plo[K] : make_float2(phi[-K].x, -phi[-K].y);
+                    float gk;
+                    float2 c;
+                    if constexpr (N1 < E / 2) {
+                        gk = lds_f32(lo + 4 * K);
+                        c = lds_f2(plo + 8 * K);
+                    } else {
+                        gk = lds_f32(hi - 4 * K);
+                        const float2 m = lds_f2(phi - 8 * K);
+                        c = make_float2(m.x, -m.y);
+                    }
                     const float2 v = cmul(x[n1], c);
                     x[n1] = make_float2(gk * v.y, gk * v.x);
                 });
@@ -558,7 +511,7 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
                 }
             }
         }
-        return true;
+        return;
     }
     if (blk * M < nsamp) {
         const int64_t obase = blk * M - D;
@@ -596,7 +549,6 @@ __device__ __forceinline__ bool ols_tile(const Src& src, int64_t tile, bool has_
             }
         }
     }
-    return true;
 }
 
 // Contiguous range of warp-tiles of warp gw out of nwarps.
@@ -624,23 +576,19 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
 
     for (int i = threadIdx.x; i < (G::TW + ph_len) / 2; i += blockDim.x)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
-    if (lane < kMaxGroups) mbar_init(reinterpret_cast<uint64_t*>(wbase) + lane, 1);
     __syncthreads();
 
-    WarpState ws{-1, false, 0u};
-    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
-                      (a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
+    WarpState ws{-1};
+    const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
-        bool ok;
         if constexpr (BATCH)
-            ok = ols_tile<N, QOVL, JobListSource, REAL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0, tw_s, a.V,
-                                   a.LV, a.overlap, wbase, lane, ws, ctl);
+            ols_tile<N, QOVL, JobListSource, REAL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0,
+                                                   tw_s, a.V, a.LV, a.overlap, wbase, lane, ws, ctl);
         else
-            ok = ols_tile<N, QOVL>(SingleJobSource{a}, tile, tile + 1 < te, 0, tw_s, a.V, a.LV,
-                                   a.overlap, wbase, lane, ws, ctl);
-        if (!ok) return;
+            ols_tile<N, QOVL>(SingleJobSource{a}, tile, tile + 1 < te, 0, tw_s, a.V, a.LV, a.overlap,
+                              wbase, lane, ws, ctl);
     }
 }
 
@@ -672,13 +620,11 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
         for (int i = threadIdx.x; i < a.plans[p].tw_len / 2; i += blockDim.x) dst[i] = srcp[i];
     }
     unsigned char* wbase = smem_raw + a.tw_bytes + (size_t)warp * a.warp_bytes;
-    if (lane < kMaxGroups) mbar_init(reinterpret_cast<uint64_t*>(wbase) + lane, 1);
     __syncthreads();
 
     const JobListSource src{a.jobs, a.tiles};
-    const TileCtl ctl{a.status, a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles, a.debug,
-                      (a.flags & kOlsNoBulk) == 0, nullptr};
-    WarpState ws{-1, false, 0u};
+    const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, nullptr};
+    WarpState ws{-1};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
@@ -687,21 +633,19 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
         const MixedPlan& P = a.plans[plan];
         const float2* tw = reinterpret_cast<const float2*>(smem_raw) + P.tw_off;
         const bool nx = tile + 1 < te;
-        bool ok = true;
         switch (P.N) {
-        case 128: ok = ols_tile<128, true>(src, tile, nx, plan, tw, P.V, P.LV, 32, wbase, lane, ws, ctl); break;
-        case 256: ok = ols_tile<256, true>(src, tile, nx, plan, tw, P.V, P.LV, 64, wbase, lane, ws, ctl); break;
-        case 512: ok = ols_tile<512, true>(src, tile, nx, plan, tw, P.V, P.LV, 128, wbase, lane, ws, ctl); break;
+        case 128: ols_tile<128, true>(src, tile, nx, plan, tw, P.V, P.LV, 32, wbase, lane, ws, ctl); break;
+        case 256: ols_tile<256, true>(src, tile, nx, plan, tw, P.V, P.LV, 64, wbase, lane, ws, ctl); break;
+        case 512: ols_tile<512, true>(src, tile, nx, plan, tw, P.V, P.LV, 128, wbase, lane, ws, ctl); break;
         default:
             if constexpr (MAXN >= 1024) {
-                if (P.N == 1024) { ok = ols_tile<1024, true>(src, tile, nx, plan, tw, P.V, P.LV, 256, wbase, lane, ws, ctl); break; }
+                if (P.N == 1024) { ols_tile<1024, true>(src, tile, nx, plan, tw, P.V, P.LV, 256, wbase, lane, ws, ctl); break; }
             }
             if constexpr (MAXN >= 2048) {
-                if (P.N == 2048) { ok = ols_tile<2048, true>(src, tile, nx, plan, tw, P.V, P.LV, 512, wbase, lane, ws, ctl); break; }
+                if (P.N == 2048) { ols_tile<2048, true>(src, tile, nx, plan, tw, P.V, P.LV, 512, wbase, lane, ws, ctl); break; }
             }
             break;
         }
-        if (!ok) return;
     }
 }
 

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const
     }
     bool ok = mbar_wait_bounded(bar, 0, kWaitLimitCycles);
     if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(status, kStatusTmaTimeout);
+        if (tid == 0) atomicOr(status, kStatusWaitTimeout);
         mbar_wait_bounded(bar, 0, kWaitLimitCycles);
     } else {
         tc_fence_after_sync();

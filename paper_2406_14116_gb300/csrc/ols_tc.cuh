@@ -205,11 +205,12 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
         __syncthreads();
         if (tid == 0) {
             tc_fence_after_sync();
-            issue_round<PREC, K>(Abuf, G::A_PIECE, Bm, b_piece, halves, tmem, bar);
+            // test hook (debug bit 0): no MMAs, so nothing arrives and the bounded wait runs out
+            if (!(a.debug & 1)) issue_round<PREC, K>(Abuf, G::A_PIECE, Bm, b_piece, halves, tmem, bar);
         }
         bool ok = mbar_wait_bounded(bar, phase, limit);
         if (!__syncthreads_and(ok)) {
-            if (tid == 0 && a.status) atomicOr(a.status, kStatusTmaTimeout);
+            if (tid == 0 && a.status) atomicOr(a.status, kStatusWaitTimeout);
             mbar_wait_bounded(bar, phase, limit);   // the MMAs may still be running: wait once more
             __syncthreads();
             return false;

@@ -178,7 +178,7 @@ struct vbw_batch_s {
 static std::mutex g_tune_mu;
 static int g_tune_warps[5] = {0, 0, 0, 0, 0};   // N = 128 << i; 0 = default
 static int g_tune_ctas[5] = {0, 0, 0, 0, 0};    // resident CTAs per SM cap; 0 = occupancy limit
-static int g_wait_limit_debug = 0;               // test hook: skip staging copies, short waits
+static int g_wait_limit_debug = 0;               // test hook: tensor-core MMAs not issued, short waits
 static int g_full_band_debug = 0;                // test hook: accept k1 = N/2 + 1 (H_R = 1)
 
 static int n_index(int N)
@@ -986,7 +986,6 @@ extern "C" vbw_status vbw_batch_create(const vbw_signal* sig, int n, vbw_batch_t
         bt->margs.nplans = nmixed;
         bt->margs.tw_bytes = (int32_t)(sizeof(float2) * (size_t)tw_off);
         bt->margs.warp_bytes = (int32_t)mixed_warp_bytes;
-        bt->margs.status = bt->groups[bt->mixed_groups[0]].plan->d_status;
     }
     if (cudaStreamCreateWithFlags(&bt->s_side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -1173,8 +1172,6 @@ static vbw_status batch_launch(vbw_batch_s* bt, cudaStream_t st, bool zero_copy 
         VBW_CUDA(cudaStreamWaitEvent(bt->s_side, bt->ev_fork, 0));
     }
     MixedArgs ma = bt->margs;
-    ma.wait_limit = g_wait_limit_debug ? 2000000LL : 0;
-    ma.debug = g_wait_limit_debug ? 1 : 0;
     ma.flags = flags;
     if (zero_copy) ma.jobs = bt->d_zmjobs;
     int grid = 0;

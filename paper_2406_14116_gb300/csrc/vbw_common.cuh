@@ -130,7 +130,7 @@ struct OlsArgs {
     int32_t LV;
     int* status;          // device status word (bit flags, e.g. a bounded wait that gave up) or nullptr
     int64_t wait_limit;   // bound of device-side waits in SM cycles (0 = default, about 2 s)
-    int32_t debug;        // test hook, bit 0: skip the staging copies (their waits then run out)
+    int32_t debug;        // test hook, bit 0: the tensor-core kernel issues no MMAs (its waits run out)
     int32_t flags;        // kOlsNoBulk: signals live in host memory, use plain loads and stores only;
                           // kOlsReal: real signals (float32), processed as pairs of blocks
     const unsigned char* tc_tables;   // tensor-core plans: DFT-matrix pieces and twiddles
@@ -158,11 +158,7 @@ struct MixedArgs {
     int32_t nplans;
     int32_t tw_bytes;     // shared bytes of all twiddle rows
     int32_t warp_bytes;   // per-warp region (largest N of the launch)
-    int32_t debug;        // as OlsArgs::debug
-    int* status;
-    int64_t wait_limit;   // as OlsArgs::wait_limit
     int32_t flags;        // as OlsArgs::flags
-    int32_t pad2_;
 };
 
 }  // namespace vbw

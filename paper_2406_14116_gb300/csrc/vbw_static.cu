@@ -4,7 +4,7 @@
 // through its own pool. A real-time loop cannot afford cudaMalloc's implicit device
 // synchronization and unbounded latency. Code may run where the CUDA allocator must not be
 // touched. The usual path needs a plan (its twiddle rows and transition table live in memory
-// that vbw_plan allocates). This entry point keeps those tables, and the kernel's status word, in
+// that vbw_plan allocates). This entry point keeps those tables in
 // one fixed array of device memory that is part of the library image. Every GPU that loads the
 // library holds that array until the process exits.
 //
@@ -39,9 +39,8 @@ constexpr size_t kVOff = kTwOff + kTwCap;    // transition table, float32: at mo
 constexpr size_t kVCap = 8192;
 constexpr size_t kVdOff = kVOff + kVCap;     // transition table as passed (double): <= 8176 bytes
 constexpr size_t kVdCap = 8192;
-constexpr size_t kStatusOff = kVdOff + kVdCap;   // device status word of the kernel
 constexpr size_t kScratchBytes = 64 * 1024;      // the whole array: 64 KiB per GPU
-static_assert(kStatusOff + sizeof(int) <= kScratchBytes, "scratch layout exceeds the array");
+static_assert(kVdOff + kVdCap <= kScratchBytes, "scratch layout exceeds the array");
 
 static __device__ __align__(256) unsigned char vbw_static_scratch[kScratchBytes];
 
@@ -107,12 +106,10 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     float2* tw = reinterpret_cast<float2*>(scratch + kTwOff);
     float* Vf = reinterpret_cast<float*>(scratch + kVOff);
     double* Vd = reinterpret_cast<double*>(scratch + kVdOff);
-    int* status = reinterpret_cast<int*>(scratch + kStatusOff);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // tables of this call (every call rewrites them), status word cleared
-    if (cudaMemcpyAsync(Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
+    // tables of this call (every call rewrites them)
+    if (cudaMemcpyAsync(Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail_static(VBW_ERR_CUDA, "table upload failed");
     const int tw_entries = T * (E + 2);
     vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
@@ -135,7 +132,6 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     a.V = Vf;
     a.overlap = overlap;
     a.LV = LV;
-    a.status = status;
     const int warps = (N <= 1024) ? 8 : 4;
     int grid = 0;
     cudaError_t e;

@@ -101,17 +101,18 @@ def test_empty_and_tiny_signals_in_batch(cuda):
             assert_parity(y.cpu().numpy(), oracle.filter(p.N, p.overlap, V, 9, x))
 
 
-@pytest.mark.parametrize("N", [512, 1024])
+@pytest.mark.parametrize("N", [256, 512])
 def test_bounded_wait_runs_out_and_reports(cuda, N):
-    """A staged copy that never arrives (test hook: the copy is not issued) makes the bounded
-    mbarrier wait run out: the kernel sets the status word and the warp returns; the context stays
-    usable and the next launch is correct. (N = 2048 blocks are not TMA-staged: no wait to run out.)"""
+    """A wait that nothing ends (test hook: the tensor-core kernel issues no MMAs, so no
+    accumulator completes) runs out after its bound: the kernel sets the status word and the CTA
+    frees its tensor memory and returns; the context stays usable and the next launch is correct.
+    (The FP32 kernels have no device-side waits.)"""
     torch = cuda
     O = N // 4
     M = N - O
-    nb = 8000                     # more blocks than resident warps, so warps stage a next block
+    nb = 8000                     # several tiles per CTA
     V = wl.transition_table(4, 12)
-    plan = vbw.Plan(N, O, V)
+    plan = vbw.Plan(N, O, V, precision=vbw.VBW_PREC_BF16_SPLIT)
     x = wl.complex_gaussian(4, 0, nb * M)
     xd = torch.from_numpy(x).cuda()
     yd = torch.zeros_like(xd)
@@ -134,7 +135,7 @@ def test_bounded_wait_runs_out_and_reports(cuda, N):
     for b0, cnt in ((0, 64), (nb // 2, 32), (nb - 64, 64)):
         ref = oracle.filter(N, O, V, 100, x, blocks=(b0, cnt))
         sl = slice(b0 * M, (b0 + cnt) * M)
-        assert_parity(y[sl], ref[sl], what=f"blocks {b0}..{b0 + cnt}")
+        assert_parity(y[sl], ref[sl], rms_tol=1e-5, elem_tol=2e-4, what=f"blocks {b0}..{b0 + cnt}")
 
 
 def test_tune_set_changes_shape_not_result(cuda):
@@ -165,8 +166,8 @@ def test_tune_set_changes_shape_not_result(cuda):
 
 def test_signals_at_odd_offsets_of_one_buffer(cuda):
     """Signals packed back to back in one device buffer start at arbitrary sample offsets, so
-    some are only 8-byte aligned: the bulk L2 prefetch and the TMA staging must skip (or realign)
-    those, and the results must not change. Also covers vbw_batch_run_host on packed buffers."""
+    some are only 8-byte aligned: the bulk L2 prefetch must realign (or skip) those, and the
+    results must not change. Also covers vbw_batch_run_host on packed buffers."""
     torch = cuda
     w = wl.mixed(seed=21, nstreams=30, log2_lo=11.0, log2_hi=14.5)
     lens = [len(s.x) for s in w.signals]

@@ -2,7 +2,7 @@
 
 Parity: the FP64 oracle filtering x + 0j (its real part) for every N, small / N/4 / N/2 overlaps,
 ragged ends, band changes on even and odd blocks (odd ones cut the signal into pieces), and
-signals at odd float offsets (no TMA staging). The result must also match the complex path on
+signals at odd float offsets (the bulk L2 prefetch realigns). The result must also match the complex path on
 x + 0j within FP32 rounding."""
 import numpy as np
 import pytest
@@ -61,7 +61,7 @@ def test_real_equals_complex_path_and_odd_offsets(cuda):
     nb = (n + M - 1) // M
     bands = wl.band_schedule(9, 0, nb, 3, 32, 480)
     buf = torch.from_numpy(np.concatenate([[0.0], x]).astype(np.float32)).cuda()
-    xd = buf[1:]                                   # 4-byte but not 16-byte aligned: no staging
+    xd = buf[1:]                                   # 4-byte but not 16-byte aligned
     yr = torch.zeros(n + 1, dtype=torch.float32, device="cuda")[1:]
     xa = torch.from_numpy(x).cuda()
     ya = torch.zeros_like(xa)
