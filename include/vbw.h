@@ -229,9 +229,9 @@ vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
  * Behaviour: as a batch of one signal (zero history, final partial block zero padded), with plan
  * geometry (N, overlap, L_V = transition samples, host doubles read during the call) and band
  * k1, on cuda_stream (a cudaStream_t, NULL = legacy stream). The caller passes device complex64
- * `in` and `out` of nsamples samples (8-byte aligned, not overlapping). The twiddle rows, the
- * float32 transition table and the kernel's status word live in one fixed 64 KiB array of device
- * memory that belongs to the library image. Every GPU that loads the library holds it until the
+ * `in` and `out` of nsamples samples (8-byte aligned, not overlapping). The twiddle rows and the
+ * float32 transition table live in one fixed 64 KiB array of device memory that belongs to the
+ * library image. Every GPU that loads the library holds it until the
  * process exits.
  *
  * The first call on a device looks up that array's device address, with the device current. Make
