@@ -237,7 +237,9 @@ static int warps_for(int N)
     }
     const int w = env_int("VBW_WARPS", 0);
     if (w == 4 || w == 8) return w;
-    return (N <= 1024) ? 8 : 4;
+    // 8-warp CTAs measured fastest for every N on GB300, N = 2048 included (one 8-warp CTA per SM
+    // at about 210 registers beat three 4-warp CTAs capped at 168 registers, which spill)
+    return 8;
 }
 
 static int ctas_cap_for(int N, int sms)

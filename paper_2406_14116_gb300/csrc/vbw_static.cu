@@ -132,7 +132,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     a.V = Vf;
     a.overlap = overlap;
     a.LV = LV;
-    const int warps = (N <= 1024) ? 8 : 4;
+    const int warps = 8;
     int grid = 0;
     cudaError_t e;
     switch (N) {

@@ -138,6 +138,34 @@ def test_bounded_wait_runs_out_and_reports(cuda, N):
         assert_parity(y[sl], ref[sl], rms_tol=1e-5, elem_tol=2e-4, what=f"blocks {b0}..{b0 + cnt}")
 
 
+def test_fp32_kernels_have_no_device_waits(cuda):
+    """The FP32 kernels wait on nothing: under the same test hook (debug bit 0, short wait limit)
+    an FP32 plan filters correctly and its status word stays clear."""
+    torch = cuda
+    N, O = 1024, 256
+    M = N - O
+    nb = 4000
+    V = wl.transition_table(5, 12)
+    plan = vbw.Plan(N, O, V)
+    x = wl.complex_gaussian(5, 0, nb * M)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    assert vbw.vbw_plan_status(plan.handle, clear=True) == 0
+    vbw.vbw_debug_set(1)
+    try:
+        s = vbw.Stream(plan, 200)
+        s.filter(xd, yd, nb)
+        torch.cuda.synchronize()
+    finally:
+        vbw.vbw_debug_set(0)
+    assert vbw.vbw_plan_status(plan.handle) == 0
+    y = yd.cpu().numpy()
+    for b0, cnt in ((0, 32), (nb - 32, 32)):
+        ref = oracle.filter(N, O, V, 200, x, blocks=(b0, cnt))
+        sl = slice(b0 * M, (b0 + cnt) * M)
+        assert_parity(y[sl], ref[sl], what=f"blocks {b0}..{b0 + cnt}")
+
+
 def test_tune_set_changes_shape_not_result(cuda):
     torch = cuda
     N, O = 512, 128
