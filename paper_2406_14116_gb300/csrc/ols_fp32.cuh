@@ -270,8 +270,9 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
 #define VBW_OLS_BOUNDS(W) __launch_bounds__((W) * 32)
 #endif
 
-// Job sources. The descriptors are re-read through opaque pointers (L1 hits) wherever they are
-// needed, so none of their fields stays live in registers across the DFT passes.
+// Job sources. A tile reads its descriptor at its start; the store keeps only the output
+// pointer, the length and the block index in registers across the DFT passes (complex signals)
+// and re-reads the rest through opaque pointers where it is needed.
 struct SingleJobSource {        // one stream segment held in the kernel parameters
     const OlsArgs& a;
     template <int B>
@@ -308,6 +309,8 @@ struct JobListSource {          // device job array + warp-tile list (batches)
 // State a warp carries from one tile to the next.
 struct WarpState {
     int table_key;        // (plan << 16) | k1 of this lane group's gain table; -1 = none
+    int2 ntd;             // N = 2048 job lists: the next tile's (job, first block), read a tile early
+    bool ntd_ok;
 };
 
 // Per-launch switches of a warp-tile.
@@ -343,12 +346,26 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
     const int SPAN = REAL ? N + M : N;                      // input samples one step reads
 
     float2 x[E];
+    float2* kout;              // kept for the store (complex signals)
+    int64_t knsamp, kblk;
     {
         // ---- which job and block this lane group works on, and its band
         OlsJob job;
         int64_t blk;
-        src.template get<B>(tile, bsub, job, blk);
+        if constexpr (std::is_same<Src, JobListSource>::value && N == 2048) {
+            // the tile list entry was read one tile early: the descriptor read starts at once
+            const int2 td = ws.ntd_ok ? ws.ntd : opaque(src.tiles)[tile];
+            job = opaque(src.jobs)[td.x];
+            blk = (int64_t)td.y + bsub;
+            ws.ntd_ok = has_next;
+            if (has_next) ws.ntd = opaque(src.tiles)[tile + 1];
+        } else {
+            src.template get<B>(tile, bsub, job, blk);
+        }
         const int64_t nsamp = job.nsamp;
+        kout = job.out;
+        knsamp = nsamp;
+        kblk = blk;
         const bool active = blk * P < nsamp;
         const int k1 = src.band(job, blk, active);
         const int key = active ? ((plan << 16) | k1) : ws.table_key;
@@ -478,11 +495,11 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
 
     // ---- discard and store (steps 4-5): z(n) = swap(x[n1]), n = T n1 + t, kept for
     //      D <= n < D + M (the exp(-j 2 pi k D / N) phase of eq. (FS_Hk_exp) as a shift)
-    OlsJob job;
-    int64_t blk;
-    src.template get<B>(tile, bsub, job, blk);
-    const int64_t nsamp = job.nsamp;
     if constexpr (REAL) {
+        OlsJob job;
+        int64_t blk;
+        src.template get<B>(tile, bsub, job, blk);
+        const int64_t nsamp = job.nsamp;
         // z(n) = swap(x[n1]): Re z -> block 2 blk, Im z -> block 2 blk + 1, kept D <= n < D + M
         if (blk * P < nsamp) {
             float* out_r = reinterpret_cast<float*>(job.out);
@@ -513,12 +530,14 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
         }
         return;
     }
+    const int64_t blk = kblk;
+    const int64_t nsamp = knsamp;
     if (blk * M < nsamp) {
         const int64_t obase = blk * M - D;
         if constexpr (QOVL) {
             // kept rows n1 in [E/8, 7E/8): every lane stores, no per-sample test when the block
             // is complete
-            float2* dst = job.out + obase + t;
+            float2* dst = kout + obase + t;
             if (obase + D + M <= nsamp) {
                 static_for<E / 8, 7 * E / 8>([&](auto n1) {
                     st_stream(dst + decltype(n1)::value * T, make_float2(x[n1].y, x[n1].x));
@@ -526,7 +545,7 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
             } else {
                 static_for<E / 8, 7 * E / 8>([&](auto n1) {
                     const int64_t oi = obase + decltype(n1)::value * T + t;
-                    if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
+                    if (oi < nsamp) st_stream(kout + oi, make_float2(x[n1].y, x[n1].x));
                 });
             }
         } else {
@@ -534,18 +553,23 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
                 const int n = decltype(n1)::value * T + t;
                 if (n >= D && n < D + M) {
                     const int64_t oi = obase + n;
-                    if (oi < nsamp) st_stream(job.out + oi, make_float2(x[n1].y, x[n1].x));
+                    if (oi < nsamp) st_stream(kout + oi, make_float2(x[n1].y, x[n1].x));
                 }
             });
         }
         // the lane group of the job's last block hands the stream's last O input samples on
-        if ((blk + 1) * M >= nsamp && job.tail_out) {
-            for (int i = t; i < O; i += T) {
-                const int64_t si = nsamp - O + i;
-                float2 v = make_float2(0.f, 0.f);
-                if (si >= 0) v = job.in[si];
-                else if (job.tail_in) v = job.tail_in[O + si];
-                job.tail_out[i] = v;
+        if ((blk + 1) * M >= nsamp) {
+            OlsJob job;
+            int64_t bj;
+            src.template get<B>(tile, bsub, job, bj);
+            if (job.tail_out) {
+                for (int i = t; i < O; i += T) {
+                    const int64_t si = nsamp - O + i;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (si >= 0) v = job.in[si];
+                    else if (job.tail_in) v = job.tail_in[O + si];
+                    job.tail_out[i] = v;
+                }
             }
         }
     }
@@ -578,7 +602,7 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
     __syncthreads();
 
-    WarpState ws{-1};
+    WarpState ws{-1, make_int2(0, 0), false};
     const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
@@ -624,7 +648,7 @@ __global__ void VBW_OLS_BOUNDS(WARPS) ols_mixed_kernel(const MixedArgs a)
 
     const JobListSource src{a.jobs, a.tiles};
     const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, nullptr};
-    WarpState ws{-1};
+    WarpState ws{-1, make_int2(0, 0), false};
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
