@@ -370,40 +370,9 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
         const int k1 = src.band(job, blk, active);
         const int key = active ? ((plan << 16) | k1) : ws.table_key;
 
-        // ---- ask L2 for the samples the warp's next tile adds (the rest is this span). The bulk
-        //      prefetch needs a 16-byte aligned start and a multiple of 16 bytes: a stream whose
-        //      base is only 8-byte aligned starts one sample later.
-        if (lane == 0 && has_next && ctl.bulk) {
-            if constexpr (REAL) {
-                const float* in_r = reinterpret_cast<const float*>(job.in);
-                int64_t e = (blk + B - 1) * P - O + SPAN;
-                int64_t e2 = e + (int64_t)B * P;
-                if (e2 > nsamp) e2 = nsamp;
-                while (e >= 0 && e < e2 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) != 0) ++e;
-                const int64_t cnt = (e2 - e) & ~int64_t(3);
-                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) == 0)
-                    prefetch_l2_bulk(in_r + e, (uint32_t)(cnt * sizeof(float)));
-            } else {
-                int64_t e = (blk + B - 1) * (int64_t)M - O + N;
-                int64_t e2 = e + (int64_t)B * M;
-                if (e2 > nsamp) e2 = nsamp;
-                if (e >= 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) != 0) ++e;
-                const int64_t cnt = (e2 - e) & ~int64_t(1);
-                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) == 0)
-                    prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
-            }
-        }
-
-        // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
-        if (__any_sync(0xffffffffu, key != ws.table_key)) {
-            __syncwarp();
-            if (active) build_gains<N>(gtab, t, k1, LV, V);
-            ws.table_key = key;
-            __syncwarp();
-        }
-
         // ---- gather x_m(n) = x(mM - O + n), n = T n1 + t (Sec. II segmentation), coalesced
-        //      loads from L2 (the span was prefetched by the warp's previous tile)
+        //      loads from L2 (the span was prefetched by the warp's previous tile). They are issued
+        //      first; the prefetch and the gain table below overlap their latency.
         const int64_t s0 = blk * P - O;
         const bool interior = active && s0 >= 0 && s0 + SPAN <= nsamp;
         if constexpr (REAL) {
@@ -449,6 +418,38 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
                 }
                 x[n1] = v;
             });
+        }
+
+        // ---- ask L2 for the samples the warp's next tile adds (the rest is this span). The bulk
+        //      prefetch needs a 16-byte aligned start and a multiple of 16 bytes: a stream whose
+        //      base is only 8-byte aligned starts one sample later.
+        if (lane == 0 && has_next && ctl.bulk) {
+            if constexpr (REAL) {
+                const float* in_r = reinterpret_cast<const float*>(job.in);
+                int64_t e = (blk + B - 1) * P - O + SPAN;
+                int64_t e2 = e + (int64_t)B * P;
+                if (e2 > nsamp) e2 = nsamp;
+                while (e >= 0 && e < e2 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) != 0) ++e;
+                const int64_t cnt = (e2 - e) & ~int64_t(3);
+                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(in_r + e) & 15) == 0)
+                    prefetch_l2_bulk(in_r + e, (uint32_t)(cnt * sizeof(float)));
+            } else {
+                int64_t e = (blk + B - 1) * (int64_t)M - O + N;
+                int64_t e2 = e + (int64_t)B * M;
+                if (e2 > nsamp) e2 = nsamp;
+                if (e >= 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) != 0) ++e;
+                const int64_t cnt = (e2 - e) & ~int64_t(1);
+                if (e >= 0 && cnt > 0 && (reinterpret_cast<uintptr_t>(job.in + e) & 15) == 0)
+                    prefetch_l2_bulk(job.in + e, (uint32_t)(cnt * sizeof(float2)));
+            }
+        }
+
+        // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
+        if (__any_sync(0xffffffffu, key != ws.table_key)) {
+            __syncwarp();
+            if (active) build_gains<N>(gtab, t, k1, LV, V);
+            ws.table_key = key;
+            __syncwarp();
         }
     }
 
