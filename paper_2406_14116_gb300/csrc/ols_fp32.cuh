@@ -309,7 +309,7 @@ struct JobListSource {          // device job array + warp-tile list (batches)
 // State a warp carries from one tile to the next.
 struct WarpState {
     int table_key;        // (plan << 16) | k1 of this lane group's gain table; -1 = none
-    int2 ntd;             // N = 2048 job lists: the next tile's (job, first block), read a tile early
+    int2 ntd;             // job lists: the next tile's (job, first block), read one tile early
     bool ntd_ok;
 };
 
@@ -352,7 +352,7 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
         // ---- which job and block this lane group works on, and its band
         OlsJob job;
         int64_t blk;
-        if constexpr (std::is_same<Src, JobListSource>::value && N == 2048) {
+        if constexpr (std::is_same<Src, JobListSource>::value) {
             // the tile list entry was read one tile early: the descriptor read starts at once
             const int2 td = ws.ntd_ok ? ws.ntd : opaque(src.tiles)[tile];
             job = opaque(src.jobs)[td.x];
