@@ -9,6 +9,8 @@ Paper passages followed (Moryakova & Johansson):
   * eq. (OLS_dn): the IDFT carries +j and 1/N.
   * eq. (FS_Hk_exp): H(k,b) = H_R(k,b) exp(-j 2 pi k (L-1)/2 / N).
   * eq. (FS_Hk_real) with the regions k_p, k_t, k_s and eq. (k_var) for k1, k2.
+  * eq. (OLS_Hn): the time-invariant response H_n of each output phase n (the PTVIR view of OLS),
+    and the error E_n of eq. (err_min) against eq. (VBW_des).
 """
 from __future__ import annotations
 
@@ -49,8 +51,9 @@ def _load():
         lib.vbwo_filter_H.argtypes = [i32, i32, p, p, i64, p, i64, i64, p, i32]
         lib.vbwo_filter.argtypes = [i32, i32, i32, p, p, p, i64, p, i64, i64, p, i32]
         lib.vbwo_max_threads.argtypes = []
+        lib.vbwo_ptvir.argtypes = [i32, i32, p, p, p, i32, p, i32]
         for f in (lib.vbwo_HR, lib.vbwo_H, lib.vbwo_dft, lib.vbwo_filter_H, lib.vbwo_filter,
-                  lib.vbwo_max_threads):
+                  lib.vbwo_max_threads, lib.vbwo_ptvir):
             f.restype = i32
         _lib = lib
     return _lib
@@ -148,3 +151,32 @@ def filter(N: int, overlap: int, V, band, x, tail=None, blocks=None, nthreads=No
     if rc != 0:
         raise ValueError(f"vbwo_filter failed ({rc})")
     return y[0::2] + 1j * y[1::2]
+
+
+def impulse_response(N: int, overlap: int, V, k1: int) -> np.ndarray:
+    """h(q) = (1/N) sum_k H(k, b) e^{+j 2 pi q k / N} (eq. OLS_dn), by the direct inverse DFT of
+    the oracle's H (complex128; real up to rounding)."""
+    return dft(H(N, overlap, V, k1), +1) / N
+
+
+def ptvir_errors_h(N: int, overlap: int, h, omega, desired, nthreads=None) -> np.ndarray:
+    """|E_n(w_i)| = |H_n(w_i) e^{j w_i O/2} - d_i| for every output phase n = 0..M-1 and grid
+    point i (eq. OLS_Hn, eq. err_min), for any impulse response h of length N. Shape (M, K)."""
+    h = np.ascontiguousarray(np.asarray(h, dtype=np.complex128))
+    if len(h) != N:
+        raise ValueError("h must have N entries")
+    omega = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    d = np.ascontiguousarray(np.broadcast_to(np.asarray(desired, dtype=np.float64), omega.shape))
+    K = len(omega)
+    M = N - overlap
+    E = np.empty((M, K), dtype=np.float64)
+    if _load().vbwo_ptvir(N, overlap, _ptr(h.view(np.float64)), _ptr(omega), _ptr(d), K, _ptr(E),
+                          _nthreads(nthreads)) != 0:
+        raise ValueError("vbwo_ptvir failed")
+    return E
+
+
+def ptvir_errors(N: int, overlap: int, V, k1: int, omega, desired, nthreads=None) -> np.ndarray:
+    """PTVIR errors |E_n(w_i, b)| (shape (M, K)) of the VBW filter with band k1 (V rounded to
+    float32, as the plan keeps it)."""
+    return ptvir_errors_h(N, overlap, impulse_response(N, overlap, V, k1), omega, desired, nthreads)

@@ -244,3 +244,37 @@ int vbwo_max_threads(void)
     return 1;
 #endif
 }
+
+/* PTVIR view of OLS (Sec. II, eq. (OLS_Hn)): output phase n = 0..M-1 of every block is a
+ * time-invariant filter. Written out from the OLS definition (Sec. II steps 1-5 with
+ * h = IDFT(H) of eq. (OLS_dn)): output sample mM + n is sample O + n of the circular convolution
+ * of the block with h, so tap q reaches the input q samples back when q <= n + O and, through the
+ * circular wrap, N - q samples ahead otherwise. Its response is
+ *     H_n(w) = sum_q h(q) exp(-j w s_n(q)),   s_n(q) = q (q <= n + O),  q - N (q > n + O).
+ * The error of eq. (err_min) against the desired response of eq. (VBW_des) with its delay
+ * (L-1)/2 = O/2 removed is E_n(w) = H_n(w) exp(j w O/2) - d.
+ * h: N complex values, interleaved (re, im). omega, d: K grid points and desired values.
+ * Writes |E_n(w_i)| to E[n * K + i] for n = 0..M-1, i = 0..K-1. Every exponential is evaluated
+ * directly from its angle, one (n, i) pair at a time. */
+int vbwo_ptvir(int N, int O, const double* h, const double* omega, const double* d, int K,
+               double* E, int nthreads)
+{
+    if (check_geometry(N, O) != 0 || K < 0) return -1;
+    const int M = N - O;
+    const double D = 0.5 * (double)O;
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int n = 0; n < M; ++n) {
+        for (int i = 0; i < K; ++i) {
+            const double w = omega[i];
+            double complex Hn = 0.0;
+            for (int q = 0; q < N; ++q) {
+                const double s = (q <= n + O) ? (double)q : (double)q - (double)N;
+                const double ang = -w * s;
+                Hn += (h[2 * q] + I * h[2 * q + 1]) * (cos(ang) + I * sin(ang));
+            }
+            const double complex e = Hn * (cos(w * D) + I * sin(w * D)) - d[i];
+            E[(size_t)n * (size_t)K + (size_t)i] = cabs(e);
+        }
+    }
+    return 0;
+}
