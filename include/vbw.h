@@ -220,6 +220,34 @@ vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A, const floa
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */
 vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
 
+/* ---- Design analysis: the PTVIR errors of the filter a plan applies ---------------------------
+ *
+ * OLS with frequency-sampled coefficients is a periodically time-varying system (Sec. II): output
+ * phase n = 0..M-1 of every block is a time-invariant filter H_n(w, b) (eq. (OLS_Hn)), and the
+ * minimax design of V (eq. (minimax), Sec. III-C) bounds the error
+ *     E_n(w, b) = H_n(w, b) e^{j w (L-1)/2} - d(w)            (eq. (err_min), eq. (VBW_des))
+ * over every phase, band and grid frequency. This call evaluates that error on the GPU for the
+ * plan's geometry (N, overlap O = L - 1) and its transition samples V (as the filter applies
+ * them, rounded to float32), building each band's impulse response h = IDFT(H) (eq. (OLS_dn)) in
+ * the kernel from (k1, V) alone.
+ *
+ * Arguments (all arrays are device memory, row-major, owned by the caller):
+ *   bands    nbands int32 values k1 (one band per row; 0 <= nbands <= 65535)
+ *   omega    nbands x K doubles: the grid frequencies w of each row, radians per sample
+ *   desired  nbands x K floats: the desired value d(w) at each point (1 passband, 0 stopband for
+ *            eq. (VBW_des); any real value is accepted)
+ *   err      nbands x K floats written: max over n of |E_n(w, b)|
+ *   phase    nbands x K int32 written: the smallest n reaching that maximum (may be NULL)
+ * A row whose k1 lies outside the range of eq. (k_var) (1 <= k1 <= N/2 - L_V - 1) gets NaN in err
+ * and -1 in phase. Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy stream); no
+ * allocation. Arithmetic is float32 with exactly reduced angles and compensated running sums: each
+ * err value is within 1e-6 x max(1, sum_q |h(q)|) of the exact modulus (measured: about 1e-7 x
+ * that sum).
+ * Errors: VBW_ERR_INVALID_ARG (null plan or array, sizes, misaligned arrays, plan of another
+ * device), VBW_ERR_CUDA (launch). */
+vbw_status vbw_ptvir_error(vbw_plan_t plan, const int* bands, int nbands, const double* omega,
+                           const float* desired, int K, float* err, int* phase, void* cuda_stream);
+
 /* Filters one whole signal without allocating anything. This is for callers that cannot
  * allocate device memory: a host framework that owns every device allocation through its own
  * pool, a real-time loop that cannot afford cudaMalloc's device synchronization and latency, or

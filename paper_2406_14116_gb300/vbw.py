@@ -96,6 +96,7 @@ def lib():
         "vbw_debug_set": [i32],
         "vbw_filter_static": [i32, i32, p, i32, i32, p, p, i64, p],
         "vbw_debug_tc_gemm": [i32, i32, i32, p, p, p],
+        "vbw_ptvir_error": [p, p, i32, p, p, i32, p, p, p],
         "vbw_server_create": [p, i32, i32, sz, i32, pp],
         "vbw_server_destroy": [p],
         "vbw_server_open_stream": [p, i32, i32, i32],
@@ -336,6 +337,30 @@ def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
     out = np.empty(N, dtype=np.float32)
     _check(lib().vbw_debug_export_HR(plan, band, _host_ptr(out)))
     return out
+
+
+def _dev_ptr_typed(x, dtype_name: str) -> int:
+    """Device pointer of a contiguous CUDA tensor of the given torch dtype name."""
+    import torch
+    if not (hasattr(x, "data_ptr") and x.is_cuda and x.is_contiguous()
+            and x.dtype == getattr(torch, dtype_name)):
+        raise ValueError(f"expected a contiguous {dtype_name} CUDA tensor")
+    return int(x.data_ptr())
+
+
+def vbw_ptvir_error(plan: int, bands, omega, desired, err, phase=None, cuda_stream=None):
+    """PTVIR errors on the GPU: bands (int32, nbands), omega (float64, nbands x K), desired
+    (float32, nbands x K); writes err (float32, nbands x K) and phase (int32, or None)."""
+    nb = int(bands.numel())
+    K = int(omega.shape[-1]) if omega.dim() == 2 else (int(omega.numel()) if nb == 1 else -1)
+    if K < 0 or omega.numel() != nb * K or desired.numel() != nb * K or err.numel() != nb * K:
+        raise ValueError("omega, desired and err must hold nbands x K values")
+    if phase is not None and phase.numel() != nb * K:
+        raise ValueError("phase must hold nbands x K values")
+    _check(lib().vbw_ptvir_error(plan, _dev_ptr_typed(bands, "int32"), nb, _dev_ptr_typed(omega, "float64"),
+                                 _dev_ptr_typed(desired, "float32"), K, _dev_ptr_typed(err, "float32"),
+                                 None if phase is None else _dev_ptr_typed(phase, "int32"),
+                                 _stream_handle(cuda_stream)))
 
 
 def _hptr(a) -> int:
