@@ -57,7 +57,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["channels", "single", "mixed", "precision", "serving", "real"],
+    ap.add_argument("--workload", choices=["channels", "single", "mixed", "precision", "serving", "real",
+                                           "ptvir"],
                     default="channels")
     ap.add_argument("--duration", type=float, default=10.0,
                     help="serving: seconds of Poisson arrivals")
@@ -963,6 +964,181 @@ def real_arm(args):
         dist.destroy_process_group()
 
 
+# PTVIR error analysis on the channel workload's geometry: every band of its range, the design
+# grid of each band (passband [0, w_c], stopband [w_s, pi])
+PTVIR = dict(seed=2, N=1024, overlap=256, LV=12, lo=32, hi=480, K=4096)
+FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 SM sub-partitions x 32)
+
+
+def ptvir_grid(N, LV, bands, K):
+    """K points per band over [0, w_c] and [w_s, pi], w_c = 2 pi (k1 - 1)/N the last passband bin,
+    w_s = 2 pi (k1 + L_V)/N the first stopband bin, in proportion to their widths."""
+    W = np.empty((len(bands), K))
+    Dd = np.empty((len(bands), K), dtype=np.float32)
+    for j, k1 in enumerate(bands):
+        wc = 2 * np.pi * (k1 - 1) / N
+        ws = 2 * np.pi * (k1 + LV) / N
+        Kp = int(np.clip(round(K * wc / (wc + np.pi - ws)), 1, K - 1))
+        W[j] = np.concatenate([np.linspace(0.0, wc, Kp), np.linspace(ws, np.pi, K - Kp)])
+        Dd[j] = np.concatenate([np.ones(Kp), np.zeros(K - Kp)])
+    return W, Dd
+
+
+def ptvir_arm(args):
+    """vbw_ptvir_error over the channel geometry's design grid: max over the M output phases of
+    |E_n(w, b)| (eq. (OLS_Hn), eq. (err_min)) at every band and grid point. The unit of work is
+    one (band, frequency) point, i.e. M error evaluations; the kernel is bound by FP32 arithmetic:
+    10 N + 11 M algorithmic flops per point (a complex phasor and a real x complex accumulation
+    per tap, a complex multiply-add and a squared modulus per phase)."""
+    import torch
+
+    from paper_2406_14116_gb300 import build as vbw_build
+    from paper_2406_14116_gb300 import vbw
+    from paper_2406_14116_gb300 import workloads as wl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    c = dict(PTVIR)
+    N, O, LV = c["N"], c["overlap"], c["LV"]
+    M = N - O
+    V = wl.transition_table(c["seed"], LV)
+    bands = np.arange(c["lo"], c["hi"] + 1, dtype=np.int32)
+    W, Dd = ptvir_grid(N, LV, bands, c["K"])
+    points = W.size
+    flops_per_point = 10 * N + 11 * M
+    cfg = {"workload": f"ptvir: N={N}, overlap {O}, L_V={LV}, k1 in {c['lo']}..{c['hi']} "
+                       f"({len(bands)} bands) x {c['K']} grid points, max over {M} output phases",
+           "N": N, "overlap": O, "L_V": LV, "bands": len(bands), "K": c["K"], "phases": M,
+           "parallelism": f"replicas x{world}",
+           "l2": "arithmetic-bound; the 22 MB of inputs stay in L2 (no flush needed)"}
+    metric = "PTVIR error evaluations |E_n(w, b)| per second (max over output phases)"
+    unit = "Gevals/s"
+
+    def oracle_leg(seconds):
+        import oracle
+        g = np.random.default_rng(3)
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < seconds:
+            j = int(g.integers(0, len(bands)))
+            cols = g.choice(W.shape[1], 4, replace=False)
+            oracle.ptvir_errors(N, O, V, int(bands[j]), W[j, cols], Dd[j, cols])
+            done += 4 * M
+        dt = time.perf_counter() - t0
+        return {"value": done / dt / 1e9, "unit": unit, "cores": oracle.max_threads(), "kind": "oracle",
+                "sample": f"{done // M} (band, frequency) points x {M} phases at seeded positions "
+                          "(FP64 direct sums over the taps, one phase at a time)", "seconds": dt}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            oracle_leg(0.5)
+        cpu = oracle_leg(max(5.0, 2.0 * args.steps))
+        print(json.dumps({"metric": metric, "value": cpu["value"], "unit": unit, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "impl": "reference", "config": cfg, "cpu_baseline": cpu,
+                          "e2e": {"value": cpu["value"], "unit": unit, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    vbw_build.build()
+    plan = vbw.Plan(N, O, V)
+    t_b = torch.tensor(bands, device="cuda")
+    t_w = torch.tensor(W, dtype=torch.float64, device="cuda")
+    t_d = torch.tensor(Dd, device="cuda")
+    t_e = torch.empty(W.shape, dtype=torch.float32, device="cuda")
+    t_p = torch.empty(W.shape, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        vbw.vbw_ptvir_error(plan.handle, t_b, t_w, t_d, t_e, t_p, side)
+    torch.cuda.synchronize()
+    steps = args.steps
+    sampler = ClockSampler(device_uuid(torch, local))
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler.start()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        ev0[k].record(side)
+        vbw.vbw_ptvir_error(plan.handle, t_b, t_w, t_d, t_e, t_p, side)
+        ev1[k].record(side)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(steps)])
+    total_ms = float(ev0[0].elapsed_time(ev1[-1]))
+    evals = points * M
+    value = rank_reduce(evals * steps / (total_ms / 1e3), "sum", "cuda") / 1e9
+    step_ms = float(per.mean())
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = 2070.0
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        try:
+            mhz = float(json.load(open(pk)).get("sm_max_mhz", mhz))
+        except Exception:
+            pass
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flops_per_point * points / (step_ms / 1e3) / 1e12
+
+    # end to end through the same call with host buffers: grid in, errors and phases out
+    e2e = None
+    if not args.no_e2e:
+        hw = torch.from_numpy(W).pin_memory()
+        hd = torch.from_numpy(Dd).pin_memory()
+        he = torch.empty(W.shape, dtype=torch.float32).pin_memory()
+        hp = torch.empty(W.shape, dtype=torch.int32).pin_memory()
+        k_e2e = max(3, min(steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(side):
+            for _ in range(k_e2e):
+                t_w.copy_(hw, non_blocking=True)
+                t_d.copy_(hd, non_blocking=True)
+                vbw.vbw_ptvir_error(plan.handle, t_b, t_w, t_d, t_e, t_p, side)
+                he.copy_(t_e, non_blocking=True)
+                hp.copy_(t_p, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": evals * k_e2e / dt / 1e9, "unit": unit,
+               "h2d_bytes_per_step": int(W.nbytes + Dd.nbytes), "d2h_bytes_per_step": int(2 * 4 * points),
+               "steps": k_e2e, "api": "pinned host grid -> device, vbw_ptvir_error, errors and phases -> host"}
+
+    cpu = None
+    worst = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        cpu = oracle_leg(args.cpu_seconds)
+        # sampled parity: the kernel's maxima against the oracle's at seeded points
+        err = t_e.cpu().numpy()
+        g = np.random.default_rng(9)
+        worst = 0.0
+        for j in g.choice(len(bands), 3, replace=False):
+            cols = g.choice(W.shape[1], 8, replace=False)
+            E = oracle.ptvir_errors(N, O, V, int(bands[j]), W[j, cols], Dd[j, cols])
+            h = oracle.impulse_response(N, O, V, int(bands[j]))
+            tol = 1e-6 * max(1.0, float(np.abs(h).sum()))
+            worst = max(worst, float(np.abs(err[j, cols] - E.max(axis=0)).max() / tol))
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
+                                        f"{mhz:.0f} MHz (maximum SM clock)",
+                         "kernel": "ptvir_error_kernel", "step_ms": step_ms,
+                         "algorithmic_flops_per_point": flops_per_point, "points_per_step": points},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": steps,
+            "max_err_over_tol_sampled": worst, "tol": "1e-6 x max(1, sum_q |h(q)|)",
+        }), flush=True)
+
+
 def vbw_tune_shape(tune, torch, N):
     c = tune.load(torch) or {}
     d = c.get("shapes", {}).get(str(N))
@@ -971,7 +1147,9 @@ def vbw_tune_shape(tune, torch, N):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.workload == "ptvir":
+        ptvir_arm(args)
+    elif args.impl == "reference":
         reference_arm(args)
     elif args.workload == "serving":
         serving_arm(args)

@@ -22,9 +22,14 @@
 //
 // Phasors e^{-j w x} (x a multiple of 1/2) come from the turn count (w / 4 pi) (2x) mod 1, split
 // into a 24-bit fixed-point part reduced exactly in integer arithmetic and a small float
-// remainder, then one sincospif per 8 taps; inside a group of 8 taps the phasor is that seed
-// times a per-thread e^{-j w l}, l < 8, seeded the same way. The running sums across groups are
-// compensated (two-sum), so the arithmetic error stays near a few float32 roundings of the terms.
+// remainder, then one sincospif per group of 16 taps. Inside a group the taps are summed against
+// a per-thread table e^{-j w l}, l < 16 (seeded the same way), and the group's seed multiplies the
+// group sum once: a tap costs two FMAs in the sums and, in the phase scan, one complex
+// multiply-add and a squared modulus. The running sums across groups are compensated (two-sum),
+// so the arithmetic error stays near a few float32 roundings of the terms.
+//
+// h is symmetric about (L-1)/2 (H_R is real and even, eq. (FS_Hk_real)): h(q) = h((O - q) mod N),
+// so the CTA evaluates the closed form once per pair of taps.
 #include <math.h>
 #include <stdint.h>
 
@@ -32,8 +37,8 @@
 
 namespace {
 
-constexpr int kPtThreads = 128;   // grid points per CTA (one per thread)
-constexpr int kGroup = 8;         // taps per phasor seed
+constexpr int kPtThreads = 256;   // grid points per CTA (one per thread)
+constexpr int kGroup = 16;        // taps per phasor seed
 
 struct PtArgs {
     int N, O, LV;
@@ -118,12 +123,14 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     float* hA = hsh;
     float* hB = hsh + pA;
     const float invn = 1.0f / static_cast<float>(N);
-    for (int idx = threadIdx.x; idx < pA + pB; idx += blockDim.x) {
-        int q;
-        bool in;
-        if (idx < pA) { q = O + 1 + idx; in = idx < nA; }
-        else          { q = idx - pA;    in = q < nB; }
-        hsh[idx] = in ? h_scaled(N, O, k1, p.LV, p.V, q) * invn : 0.f;
+    for (int idx = threadIdx.x; idx < pA + pB; idx += blockDim.x)   // the padding
+        if ((idx < pA && idx >= nA) || (idx >= pA && idx - pA >= nB)) hsh[idx] = 0.f;
+    // taps q with 2q - O in [0, N] (q = (O + a)/2), each written with its mirror q' = (O - q) mod N
+    for (int q = (O + 1) / 2 + threadIdx.x; 2 * q - O <= N && q < N; q += blockDim.x) {
+        const float v = h_scaled(N, O, k1, p.LV, p.V, q) * invn;
+        const int qm = ((O - q) % N + N) % N;
+        hsh[q > O ? q - (O + 1) : pA + q] = v;
+        hsh[qm > O ? qm - (O + 1) : pA + qm] = v;
     }
     __syncthreads();
     if (i >= p.K) return;
@@ -145,31 +152,31 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     float Rx = 0.f, Ry = 0.f, Rcx = 0.f, Rcy = 0.f;
     for (int c0 = 0; c0 < pA; c0 += kGroup) {
         const float2 base = phasor(n1, g2, O + 2 + 2 * c0);
-        float lx = 0.f, ly = 0.f;
+        float qx = 0.f, qy = 0.f;
 #pragma unroll
         for (int l = 0; l < kGroup; ++l) {
-            const float2 ph = cmulf(base, rot[l]);
             const float hv = hA[c0 + l];
-            lx = fmaf(hv, ph.x, lx);
-            ly = fmaf(hv, ph.y, ly);
+            qx = fmaf(hv, rot[l].x, qx);
+            qy = fmaf(hv, rot[l].y, qy);
         }
-        two_sum_add(Rx, Rcx, lx);
-        two_sum_add(Ry, Rcy, ly);
+        const float2 loc = cmulf(base, make_float2(qx, qy));
+        two_sum_add(Rx, Rcx, loc.x);
+        two_sum_add(Ry, Rcy, loc.y);
     }
     // P0 = sum_{q <= O} a_q, 2 (q - O/2) = 2 q - O
     float Px = 0.f, Py = 0.f, Pcx = 0.f, Pcy = 0.f;
     for (int c0 = 0; c0 < pB; c0 += kGroup) {
         const float2 base = phasor(n1, g2, 2 * c0 - O);
-        float lx = 0.f, ly = 0.f;
+        float qx = 0.f, qy = 0.f;
 #pragma unroll
         for (int l = 0; l < kGroup; ++l) {
-            const float2 ph = cmulf(base, rot[l]);
             const float hv = hB[c0 + l];
-            lx = fmaf(hv, ph.x, lx);
-            ly = fmaf(hv, ph.y, ly);
+            qx = fmaf(hv, rot[l].x, qx);
+            qy = fmaf(hv, rot[l].y, qy);
         }
-        two_sum_add(Px, Pcx, lx);
-        two_sum_add(Py, Pcy, ly);
+        const float2 loc = cmulf(base, make_float2(qx, qy));
+        two_sum_add(Px, Pcx, loc.x);
+        two_sum_add(Py, Pcy, loc.y);
     }
     const float2 ewn = phasor(n1, g2, -2 * N);                    // e^{+j w N}
     const float2 R = make_float2(Rx + Rcx, Ry + Rcy);
@@ -180,27 +187,40 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     // phase n = 0 (p = O): A = 0
     float best = alpha.x * alpha.x + alpha.y * alpha.y;
     int arg = 0;
-    // phases n = 1 .. M - 1 (p = O + n): A(p) = sum of a_q, O < q <= p; padded taps add zero and
-    // repeat the previous phase's value, which never replaces it (strict comparison)
+    // phases n = 1 .. M - 1 (p = O + n): A(p) = sum of a_q, O < q <= p, i.e. the sum before the
+    // group plus base * Q_l with Q_l = sum_{i <= l} h e^{-j w i}; padded taps add zero and repeat
+    // the previous phase's value, which never replaces it (the first maximum is kept)
     float Ax = 0.f, Ay = 0.f, Acx = 0.f, Acy = 0.f;
     for (int c0 = 0; c0 < pA; c0 += kGroup) {
         const float2 base = phasor(n1, g2, O + 2 + 2 * c0);
         const float2 A = make_float2(Ax + Acx, Ay + Acy);
         const float2 ac = make_float2(alpha.x + (u.x * A.x - u.y * A.y), alpha.y + (u.x * A.y + u.y * A.x));
-        float lx = 0.f, ly = 0.f;
+        const float2 ub = cmulf(u, base);
+        float qx = 0.f, qy = 0.f;
+        float m2[kGroup];
 #pragma unroll
         for (int l = 0; l < kGroup; ++l) {
-            const float2 ph = cmulf(base, rot[l]);
             const float hv = hA[c0 + l];
-            lx = fmaf(hv, ph.x, lx);
-            ly = fmaf(hv, ph.y, ly);
-            const float ex = fmaf(u.x, lx, fmaf(-u.y, ly, ac.x));
-            const float ey = fmaf(u.x, ly, fmaf(u.y, lx, ac.y));
-            const float m2 = fmaf(ex, ex, ey * ey);
-            if (m2 > best) { best = m2; arg = c0 + l + 1; }
+            qx = fmaf(hv, rot[l].x, qx);
+            qy = fmaf(hv, rot[l].y, qy);
+            const float ex = fmaf(ub.x, qx, fmaf(-ub.y, qy, ac.x));
+            const float ey = fmaf(ub.x, qy, fmaf(ub.y, qx, ac.y));
+            m2[l] = fmaf(ex, ex, ey * ey);
         }
-        two_sum_add(Ax, Acx, lx);
-        two_sum_add(Ay, Acy, ly);
+        float gmax = m2[0];
+#pragma unroll
+        for (int l = 1; l < kGroup; ++l) gmax = fmaxf(gmax, m2[l]);
+        if (gmax > best) {
+            int first = kGroup - 1;
+#pragma unroll
+            for (int l = kGroup - 1; l >= 0; --l)
+                if (m2[l] == gmax) first = l;
+            best = gmax;
+            arg = c0 + first + 1;
+        }
+        const float2 loc = cmulf(base, make_float2(qx, qy));
+        two_sum_add(Ax, Acx, loc.x);
+        two_sum_add(Ay, Acy, loc.y);
     }
     p.err[at] = sqrtf(best);
     if (p.phase) p.phase[at] = arg;

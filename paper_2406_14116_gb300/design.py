@@ -177,6 +177,123 @@ def design_transition(N: int, L: int, Delta_N: int, bN_lo: int, bN_hi: int, K: i
                   bN=(bN_lo, bN_hi), iterations=it)
 
 
+def candidate_rows(N: int, L: int, LV: int, k1: np.ndarray, n: np.ndarray, omega: np.ndarray,
+                   d: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(A, c) with E = A V + c for a list of (band k1, output phase n, frequency w, desired d)
+    points, in FP64: the rows of eq. (minimax) at those points only (same responses as
+    phase_responses). A is (P, L_V) complex, c (P,) complex."""
+    O = L - 1
+    D = O / 2.0
+    q = np.arange(N)
+    P = len(k1)
+    A = np.empty((P, LV), dtype=np.complex128)
+    c = np.empty(P, dtype=np.complex128)
+    for kk in np.unique(k1):
+        sel = np.nonzero(k1 == kk)[0]
+        C = h_basis(N, L, int(kk), LV)                                   # (N, L_V + 1)
+        s = np.where(q[None, :] <= n[sel, None] + O, q[None, :], q[None, :] - N)
+        F = np.exp(-1j * omega[sel, None] * (s - D)) @ C                 # (p, L_V + 1)
+        A[sel] = F[:, 1:]
+        c[sel] = F[:, 0] - d[sel]
+    return A, c
+
+
+def design_transition_gpu(N: int, L: int, Delta_N: int, bN_lo: int, bN_hi: int, K: int = 1000,
+                          tol: float = 1e-3, max_iter: int = 500, cuts: int = 500,
+                          check: int = 4000) -> Design:
+    """eq. (minimax) as design_transition, with the search over (band, phase, frequency) on the GPU.
+
+    Each round, the kernel behind vbw_ptvir_error evaluates max_n |E_n(w, b)| at every grid point
+    of every band for the current V (float32, within about 1e-7 x sum |h| of the exact value) and
+    returns the phase reaching it. The `check` largest points are then re-evaluated in FP64 on the
+    host (candidate_rows) and the violated ones give the LP's new half-planes, as in
+    design_transition. Stops when the FP64 maximum over those points is within `tol` (relative)
+    of the LP's bound; the returned delta is that FP64 maximum. No matrix over every point is
+    formed, so the grid size is bounded by device memory, not by host memory."""
+    import torch
+    from scipy.optimize import linprog
+
+    from . import vbw
+
+    LV = Delta_N - 1
+    O = L - 1
+    bNs = list(range(bN_lo, bN_hi + 1))
+    k1s = []
+    ws, ds = [], []
+    for bN in bNs:
+        k1, k2 = band_bins(bN, Delta_N)
+        if k1 < 1 or k2 > N // 2 - 2:
+            raise ValueError(f"b_N={bN} outside the range eq. (k_var) allows for N={N}")
+        w, d = grid(bN, Delta_N, N, K)
+        k1s.append(k1)
+        ws.append(w)
+        ds.append(d)
+    Kmax = max(len(w) for w in ws)
+    # rows of equal length: a short row repeats its last point (evaluated twice, harmless)
+    W = np.stack([np.concatenate([w, np.full(Kmax - len(w), w[-1])]) for w in ws])
+    Dd = np.stack([np.concatenate([d, np.full(Kmax - len(d), d[-1])]) for d in ds])
+    dev = torch.device("cuda")
+    t_bands = torch.tensor(np.asarray(k1s, np.int32), device=dev)
+    t_w = torch.tensor(W, dtype=torch.float64, device=dev)
+    t_d = torch.tensor(Dd.astype(np.float32), device=dev)
+    t_err = torch.empty(W.shape, dtype=torch.float32, device=dev)
+    t_ph = torch.empty(W.shape, dtype=torch.int32, device=dev)
+    k1_arr = np.asarray(k1s)
+
+    def worst_points(V):
+        plan = vbw.Plan(N, O, V)
+        try:
+            vbw.vbw_ptvir_error(plan.handle, t_bands, t_w, t_d, t_err, t_ph)
+            torch.cuda.synchronize()
+        finally:
+            plan.close()
+        err = t_err.cpu().numpy().ravel()
+        top = np.argpartition(err, -min(check, err.size))[-min(check, err.size):]
+        r, col = np.divmod(top, Kmax)
+        n = t_ph.cpu().numpy().ravel()[top]
+        A, c = candidate_rows(N, L, LV, k1_arr[r], n, W[r, col], Dd[r, col])
+        return A, c
+
+    rows_A, rows_b = [], []
+
+    def add(A, c, th):
+        e = np.exp(-1j * th)
+        rows_A.append(np.hstack([(e[:, None] * A).real, -np.ones((len(c), 1))]))
+        rows_b.append(-(e * c).real)
+
+    # start: the worst points of a linear transition, eight half-planes each
+    V = np.linspace(1.0, 0.0, LV + 2)[1:-1]
+    A, c = worst_points(V)
+    take = np.argsort(np.abs(A @ V + c))[::-1][:cuts]
+    for t in np.arange(8) * (np.pi / 4):
+        add(A[take], c[take], np.full(len(take), t))
+    cost = np.zeros(LV + 1)
+    cost[-1] = 1.0
+    bounds = [(None, None)] * LV + [(0, None)]
+    it = 0
+    worst = np.inf
+    for it in range(1, max_iter + 1):
+        A_ub, b_ub = np.vstack(rows_A), np.concatenate(rows_b)
+        res = linprog(cost, A_ub=A_ub, b_ub=b_ub, bounds=bounds, method="highs")
+        if res.status != 0:
+            raise RuntimeError(f"LP failed: {res.message}")
+        V, lp_delta = res.x[:LV], res.x[-1]
+        A, c = worst_points(V)
+        E = A @ V + c
+        mag = np.abs(E)
+        worst = mag.max()
+        if worst <= lp_delta * (1 + tol) + 1e-15:
+            break
+        if it % 5 == 0:
+            keep = (b_ub - A_ub @ res.x) < 0.5 * lp_delta
+            rows_A, rows_b = [A_ub[keep]], [b_ub[keep]]
+        viol = np.nonzero(mag > lp_delta * (1 + tol))[0]
+        take = viol[np.argsort(mag[viol])[::-1][:cuts]]
+        add(A[take], c[take], np.angle(E[take]))
+    return Design(V=V, delta=float(worst), N=N, L=L, M=N - L + 1, Delta_N=Delta_N,
+                  bN=(bN_lo, bN_hi), iterations=it)
+
+
 def design_procedure(Delta: float, delta_E: float, b_lo: float, b_hi: float, K: int = 1000,
                      delta_p: float | None = None, delta_s: float | None = None):
     """The design procedure of Sec. III-D: estimate N_D (eq. (filt_order_estim)) and N, solve
