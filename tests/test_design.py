@@ -74,3 +74,20 @@ def test_design_procedure_meets_the_specification():
     # one order lower than the returned one fails the specification
     lower = design.design_transition(d.N, d.L - 2, d.Delta_N, *d.bN)
     assert lower.delta > 1e-3
+
+
+def test_candidate_rows_equal_the_full_responses():
+    """The GPU-search designer builds LP rows only at the points the GPU reports; those rows must
+    be the full error system's rows at the same (band, phase, frequency)."""
+    N, L, LV = 64, 17, 6
+    M = N - L + 1
+    g = np.random.default_rng(3)
+    for k1 in (3, 12):
+        w = g.uniform(0, np.pi, 7)
+        d = (g.uniform(0, 1, 7) < 0.5).astype(float)
+        F = design.phase_responses(design.h_basis(N, L, k1, LV), N, L, w)   # (M, K, LV + 1)
+        n = g.integers(0, M, 20)
+        i = g.integers(0, 7, 20)
+        A, c = design.candidate_rows(N, L, LV, np.full(20, k1), n, w[i], d[i])
+        np.testing.assert_allclose(A, F[n, i, 1:], atol=1e-14)
+        np.testing.assert_allclose(c, F[n, i, 0] - d[i], atol=1e-14)
