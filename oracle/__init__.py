@@ -11,6 +11,7 @@ Paper passages followed (Moryakova & Johansson):
   * eq. (FS_Hk_real) with the regions k_p, k_t, k_s and eq. (k_var) for k1, k2.
   * eq. (OLS_Hn): the time-invariant response H_n of each output phase n (the PTVIR view of OLS),
     and the error E_n of eq. (err_min) against eq. (VBW_des).
+  * Sec. I / Sec. II: overlap-add, the other FC method, with the same H(k) and the same steps 1-3.
 """
 from __future__ import annotations
 
@@ -52,8 +53,10 @@ def _load():
         lib.vbwo_filter.argtypes = [i32, i32, i32, p, p, p, i64, p, i64, i64, p, i32]
         lib.vbwo_max_threads.argtypes = []
         lib.vbwo_ptvir.argtypes = [i32, i32, p, p, p, i32, p, i32]
+        lib.vbwo_filter_ola.argtypes = [i32, i32, i32, p, p, p, i64, p]
+        lib.vbwo_filter_ola_H.argtypes = [i32, i32, p, p, i64, p]
         for f in (lib.vbwo_HR, lib.vbwo_H, lib.vbwo_dft, lib.vbwo_filter_H, lib.vbwo_filter,
-                  lib.vbwo_max_threads, lib.vbwo_ptvir):
+                  lib.vbwo_max_threads, lib.vbwo_ptvir, lib.vbwo_filter_ola, lib.vbwo_filter_ola_H):
             f.restype = i32
         _lib = lib
     return _lib
@@ -180,3 +183,38 @@ def ptvir_errors(N: int, overlap: int, V, k1: int, omega, desired, nthreads=None
     """PTVIR errors |E_n(w_i, b)| (shape (M, K)) of the VBW filter with band k1 (V rounded to
     float32, as the plan keeps it)."""
     return ptvir_errors_h(N, overlap, impulse_response(N, overlap, V, k1), omega, desired, nthreads)
+
+
+def filter_ola(N: int, overlap: int, V, band, x) -> np.ndarray:
+    """Overlap-add VBW filtering (Sec. I, Sec. II steps 1-3 on zero-padded blocks of M = N - O
+    samples, results overlapped by O and added) of a complex64 signal; ``band`` is k1 per block
+    (an int applies to all). Returns complex128 output of the input's length."""
+    x = _c64(x)
+    T = len(x)
+    M = N - overlap
+    nblocks = (T + M - 1) // M
+    band = np.asarray(band, dtype=np.int32)
+    if band.ndim == 0:
+        band = np.full(max(nblocks, 1), int(band), dtype=np.int32)
+    band = np.ascontiguousarray(band)
+    if len(band) < nblocks:
+        raise ValueError("band must have one entry per block")
+    V = _f32(V)
+    y = np.empty(2 * T, dtype=np.float64)
+    rc = _load().vbwo_filter_ola(N, overlap, len(V), _ptr(V), _ptr(band), _ptr(x.view(np.float32)), T,
+                                 _ptr(y))
+    if rc != 0:
+        raise ValueError(f"vbwo_filter_ola failed ({rc})")
+    return y[0::2] + 1j * y[1::2]
+
+
+def filter_ola_H(N: int, overlap: int, Hk, x) -> np.ndarray:
+    """Overlap-add filtering with one fixed complex H(k) for every block (complex128 output)."""
+    x = _c64(x)
+    T = len(x)
+    Hk = np.ascontiguousarray(np.asarray(Hk, dtype=np.complex128))
+    y = np.empty(2 * T, dtype=np.float64)
+    if _load().vbwo_filter_ola_H(N, overlap, _ptr(Hk.view(np.float64)), _ptr(x.view(np.float32)), T,
+                                 _ptr(y)) != 0:
+        raise ValueError("vbwo_filter_ola_H failed")
+    return y[0::2] + 1j * y[1::2]

@@ -278,3 +278,85 @@ int vbwo_ptvir(int N, int O, const double* h, const double* omega, const double*
     }
     return 0;
 }
+
+/* Overlap-add (OLA) fast convolution, the FC method the paper names beside OLS (Sec. I): the
+ * input is cut into non-overlapping blocks u_m(i) = x(mM + i), i = 0..M-1, each zero padded to N
+ * samples; each block goes through the same steps 1-3 of Sec. II (N-point DFT, multiply by H(k),
+ * N-point IDFT with 1/N); the N-sample results overlap by N - M = O samples and are added:
+ *     y(t) = sum_m z_m(t - mM),  0 <= t - mM < N.
+ * Samples past the end of x are zero; y is written for t = 0..T-1. band[m] is k1 of block m and
+ * H(k, band[m]) is built as in vbwo_filter (eq. (FS_Hk_exp)/(FS_Hk_real)). Sequential over
+ * blocks (the additions of overlapping blocks are done in block order). */
+/* One OLA block m with coefficients H (N complex): adds z_m(n) to y(mM + n) for mM + n < T. */
+static void ola_block(int N, int O, const double complex* H, const double complex* fwd,
+                      const double complex* inv, const float* x, int64_t T, int64_t m, double* y,
+                      double complex* work)
+{
+    const int M = N - O;
+    double complex* u = work;
+    double complex* X = work + N;
+    double complex* z = work + 2 * N;
+    for (int i = 0; i < N; ++i) {                      /* u_m: M samples, zero padded */
+        const int64_t s = m * (int64_t)M + i;
+        u[i] = (i < M && s < T) ? (x[2 * s] + I * x[2 * s + 1]) : 0.0;
+    }
+    direct_dft(N, fwd, u, X);                          /* step 1 */
+    for (int k = 0; k < N; ++k) X[k] *= H[k];          /* step 2 */
+    direct_dft(N, inv, X, z);                          /* step 3 with 1/N */
+    for (int n = 0; n < N; ++n) {                      /* overlap and add */
+        const int64_t t = m * (int64_t)M + n;
+        if (t >= T) break;
+        y[2 * t] += creal(z[n]) / (double)N;
+        y[2 * t + 1] += cimag(z[n]) / (double)N;
+    }
+}
+
+static int ola_run(int N, int O, const double* Hfixed, int LV, const float* V, const int32_t* band,
+                   const float* x, int64_t T, double* y)
+{
+    if (check_geometry(N, O) != 0 || O == 0 || T < 0) return -1;
+    const int M = N - O;
+    const int64_t nblocks = (T + M - 1) / M;
+    if (!Hfixed) {
+        for (int64_t m = 0; m < nblocks; ++m) {
+            const int k1 = band[m];
+            if (k1 < 1 || k1 + LV - 1 > N / 2 - 2) return -2;
+        }
+    }
+    double complex* fwd = (double complex*)malloc(sizeof(double complex) * (size_t)N);
+    double complex* inv = (double complex*)malloc(sizeof(double complex) * (size_t)N);
+    double complex* work = (double complex*)malloc(sizeof(double complex) * 3 * (size_t)N);
+    double complex* H = (double complex*)malloc(sizeof(double complex) * (size_t)N);
+    double* Hri = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    if (!fwd || !inv || !work || !H || !Hri) {
+        free(fwd); free(inv); free(work); free(H); free(Hri);
+        return -1;
+    }
+    unit_roots(N, -1, fwd);
+    unit_roots(N, +1, inv);
+    for (int64_t t = 0; t < 2 * T; ++t) y[t] = 0.0;
+    for (int64_t m = 0; m < nblocks; ++m) {
+        if (Hfixed) {
+            for (int k = 0; k < N; ++k) H[k] = Hfixed[2 * k] + I * Hfixed[2 * k + 1];
+        } else {
+            vbwo_H(N, O, LV, V, band[m], Hri);
+            for (int k = 0; k < N; ++k) H[k] = Hri[2 * k] + I * Hri[2 * k + 1];
+        }
+        ola_block(N, O, H, fwd, inv, x, T, m, y, work);
+    }
+    free(fwd); free(inv); free(work); free(H); free(Hri);
+    return 0;
+}
+
+/* OLA with the VBW coefficients H(k, band[m]) of eq. (FS_Hk_exp)/(FS_Hk_real) for block m. */
+int vbwo_filter_ola(int N, int O, int LV, const float* V, const int32_t* band, const float* x,
+                    int64_t T, double* y)
+{
+    return ola_run(N, O, NULL, LV, V, band, x, T, y);
+}
+
+/* OLA with one fixed complex H (2N interleaved doubles) for every block. */
+int vbwo_filter_ola_H(int N, int O, const double* Hri, const float* x, int64_t T, double* y)
+{
+    return ola_run(N, O, Hri, 0, NULL, NULL, x, T, y);
+}
