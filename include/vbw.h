@@ -220,6 +220,30 @@ vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A, const floa
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */
 vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
 
+/* ---- Overlap-add: the other fast-convolution method -----------------------------------------
+ *
+ * Sec. I names overlap-save (OLS) and overlap-add (OLA) as the two fast-convolution methods and
+ * chooses OLS. This call filters with OLA and the same coefficients H(k, b) (eq. (FS_Hk_exp),
+ * eq. (FS_Hk_real)): block m takes the M = N - O input samples x(mM .. mM + M - 1), zero padded
+ * to N, through the N-point DFT, the multiply by H and the N-point IDFT with 1/N (Sec. II steps
+ * 1-3); the N-sample results overlap by O and are added:
+ *     y(t) = sum_m z_m(t - mM),  0 <= t - mM < N,
+ * written for t = 0..nsamples-1 (samples past the end are zero, the last block's tail beyond the
+ * signal is dropped). Like OLS with the frequency-sampled H, OLA is periodically time-varying; the
+ * two outputs differ by their aliasing terms and agree exactly when h = IDFT(H) has length L = O + 1.
+ *
+ * Arguments: plan (FP32 precision, even overlap O <= N/2, else VBW_ERR_UNSUPPORTED); in, out:
+ * device complex64, nsignals rows of nsamples samples each, back to back (8-byte aligned, not
+ * overlapping); band: k1 of every block, checked against the plan (eq. (k_var)), used when
+ * band_per_block is NULL; band_per_block: device int32, nsignals x ceil(nsamples / M) values of k1
+ * (row-major, 4-byte aligned), or NULL. Values of band_per_block are not checked: a k1 outside
+ * eq. (k_var)'s range gives that block other gains (the kernel still reads only V). Whole signals
+ * only (no stream state); asynchronous on cuda_stream (a cudaStream_t, NULL = legacy stream); no
+ * allocation.
+ * Errors: VBW_ERR_INVALID_ARG, VBW_ERR_BAND_RANGE, VBW_ERR_UNSUPPORTED, VBW_ERR_CUDA. */
+vbw_status vbw_filter_ola(vbw_plan_t plan, const void* in, void* out, int64_t nsamples, int nsignals,
+                          int band, const int* band_per_block, void* cuda_stream);
+
 /* ---- Design analysis: the PTVIR errors of the filter a plan applies ---------------------------
  *
  * OLS with frequency-sampled coefficients is a periodically time-varying system (Sec. II): output

@@ -97,6 +97,7 @@ def lib():
         "vbw_filter_static": [i32, i32, p, i32, i32, p, p, i64, p],
         "vbw_debug_tc_gemm": [i32, i32, i32, p, p, p],
         "vbw_ptvir_error": [p, p, i32, p, p, i32, p, p, p],
+        "vbw_filter_ola": [p, p, p, i64, i32, i32, p, p],
         "vbw_server_create": [p, i32, i32, sz, i32, pp],
         "vbw_server_destroy": [p],
         "vbw_server_open_stream": [p, i32, i32, i32],
@@ -337,6 +338,15 @@ def vbw_debug_export_HR(plan: int, band: int) -> np.ndarray:
     out = np.empty(N, dtype=np.float32)
     _check(lib().vbw_debug_export_HR(plan, band, _host_ptr(out)))
     return out
+
+
+def vbw_filter_ola(plan: int, inp, out, nsamples: int, nsignals: int = 1, band: int = 0,
+                   band_per_block=None, cuda_stream=None):
+    """Overlap-add filtering of nsignals back-to-back complex64 rows (device tensors); band_per_block
+    is an int32 CUDA tensor of nsignals x ceil(nsamples / M) k1 values, or None."""
+    bpb = None if band_per_block is None else _dev_ptr_typed(band_per_block, "int32")
+    _check(lib().vbw_filter_ola(plan, _dev_ptr(inp), _dev_ptr(out), nsamples, nsignals, band, bpb,
+                                _stream_handle(cuda_stream)))
 
 
 def _dev_ptr_typed(x, dtype_name: str) -> int:
