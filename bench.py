@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["channels", "single", "mixed", "precision", "serving", "real",
-                                           "ptvir"],
+                                           "ptvir", "ola"],
                     default="channels")
     ap.add_argument("--duration", type=float, default=10.0,
                     help="serving: seconds of Poisson arrivals")
@@ -79,6 +79,7 @@ def parse_args():
 
 
 KERNEL_SOURCES = ("ols_fp32.cuh", "fft_reg.cuh", "vbw_common.cuh")   # the fused FP32 kernel
+OLA_SOURCES = KERNEL_SOURCES + ("vbw_ola.cu",)                        # the overlap-add kernel
 
 
 # ---- cross-rank reductions (replicas: each rank runs its own streams; no data-path collective)
@@ -105,15 +106,16 @@ def job_gsamples(samples_per_rank: int, steps: int, seconds_per_rank: float, dev
     return samples_per_rank * _group_size() * steps / slowest / 1e9
 
 
-def source_hash() -> str:
-    """Hash of the sources that define the fused FP32 kernel (profiles record it)."""
+def source_hash(files=None) -> str:
+    """Hash of the sources that define a kernel (default: the fused FP32 OLS kernel); profiles
+    record it."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (files or KERNEL_SOURCES):
         h.update(open(os.path.join(ROOT, "paper_2406_14116_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
 
-def profile_traffic(kernel_tag: str):
+def profile_traffic(kernel_tag: str, files=None):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on this source."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
@@ -121,7 +123,7 @@ def profile_traffic(kernel_tag: str):
     text = open(path).read()
     m_h = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     m_t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    if not m_h or not m_t or m_h.group(1) != source_hash():
+    if not m_h or not m_t or m_h.group(1) != source_hash(files):
         return None
     return float(m_t.group(1))
 
@@ -1139,6 +1141,162 @@ def ptvir_arm(args):
         }), flush=True)
 
 
+def ola_reference(args):
+    """The FP64 OLA oracle on the OLA workload's geometry, timed on the host cores: each step one
+    run of consecutive blocks of a seeded signal (the reference arm of --workload ola)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2406_14116_gb300 import workloads as wl
+    c = CHANNELS
+    N, O = c["N"], c["overlap"]
+    M = N - O
+    V = wl.transition_table(c["seed"], c["LV"])
+    nblk = 24
+    x = wl.complex_gaussian(c["seed"], 0, nblk * M)
+    bands = wl.band_schedule(c["seed"], 0, nblk, c["every"], c["lo"], c["hi"])
+    for _ in range(args.warmup):
+        oracle.filter_ola(N, O, V, bands, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.filter_ola(N, O, V, bands, x)
+    dt = time.perf_counter() - t0
+    value = len(x) * args.steps / dt / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"ola: N={N}, overlap {O}, L_V={c['LV']}, one signal of {nblk} blocks per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {nblk} consecutive blocks of one signal (FP64 direct-DFT OLA)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def ola_arm(args):
+    """The channel workload (64 x 2^22 complex64, N=1024, overlap 256, bands redrawn every 16
+    blocks) through vbw_filter_ola: overlap-add with the same coefficients, one launch per step.
+    16 algorithmic bytes per output sample, as for OLS."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_14116_gb300 import build as vbw_build
+    from paper_2406_14116_gb300 import vbw
+    from paper_2406_14116_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vbw_build.build()
+    c = dict(CHANNELS)
+    if args.channels:
+        c["nch"] = args.channels
+    if args.samples:
+        c["nsamples"] = args.samples
+    N, O, nch, T = c["N"], c["overlap"], c["nch"], c["nsamples"]
+    M = N - O
+    V = wl.transition_table(c["seed"], c["LV"])
+    nb = (T + M - 1) // M
+    g = torch.Generator(device="cuda").manual_seed(c["seed"] * 1000 + 17 + rank)
+    x = torch.randn((nch, T), dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    bands_np = np.stack([wl.band_schedule(c["seed"], i, nb, c["every"], c["lo"], c["hi"]) for i in range(nch)])
+    bands = torch.from_numpy(bands_np.astype(np.int32)).cuda()
+    plan = vbw.Plan(N, O, V)
+    side = torch.cuda.Stream()
+
+    def step():
+        vbw.vbw_filter_ola(plan.handle, x, y, T, nch, 0, bands, side)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device_uuid(torch, local))
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler.start()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        ev0[k].record(side)
+        step()
+        ev1[k].record(side)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)])
+    total_ms = float(ev0[0].elapsed_time(ev1[-1]))
+    total = nch * T
+    value = job_gsamples(total, args.steps, total_ms / 1e3, "cuda")
+    step_ms = float(per.mean())
+    peak, peak_src = measured_peaks()
+    achieved = BYTES_PER_SAMPLE * total / (step_ms / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        hx = x.cpu().pin_memory()
+        hy = torch.empty_like(hx, pin_memory=True)
+        k_e2e = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(side):
+            for _ in range(k_e2e):
+                x.copy_(hx, non_blocking=True)
+                step()
+                hy.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": job_gsamples(total, k_e2e, dt, "cuda"), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "steps": k_e2e,
+               "api": "pinned host -> device copy, vbw_filter_ola, device -> host copy"}
+
+    cpu = None
+    rms = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(7)
+        t0 = time.perf_counter()
+        num = den = 0.0
+        done = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            i = int(rng.integers(0, nch))
+            b0 = int(rng.integers(1, max(2, nb - 16)))
+            lo, hi = (b0 - 1) * M, min(T, (b0 + 16) * M)
+            xs = x[i, lo:hi].cpu().numpy()
+            ref = oracle.filter_ola(N, O, V, bands_np[i][b0 - 1:], xs)[M:]
+            got = y[i, b0 * M:hi].cpu().numpy().astype(np.complex128)
+            num += float(np.sum(np.abs(got - ref) ** 2))
+            den += float(np.sum(np.abs(ref) ** 2))
+            done += hi - b0 * M
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} output samples in runs of 16 blocks at seeded positions (FP64 direct-DFT "
+                         "OLA, sequential)", "seconds": dt}
+        rms = math.sqrt(num / den) if den > 0 else None
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ola: {nch} x {T} complex64, N={N}, overlap {O}, L_V={c['LV']}, "
+                                   f"k1~U{{{c['lo']}..{c['hi']}}} every {c['every']} blocks; overlap-add",
+                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": profile_traffic("ola_fp32_n1024_channels", OLA_SOURCES),
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)", "kernel": "ola_fp32_kernel",
+                         "step_ms": step_ms, "algorithmic_bytes_per_step": BYTES_PER_SAMPLE * total},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
+            "rms_rel_err_sampled": rms, "rms_tol": FP32_RMS_TOL,
+        }), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def vbw_tune_shape(tune, torch, N):
     c = tune.load(torch) or {}
     d = c.get("shapes", {}).get(str(N))
@@ -1149,6 +1307,8 @@ def main():
     args = parse_args()
     if args.workload == "ptvir":
         ptvir_arm(args)
+    elif args.workload == "ola":
+        ola_reference(args) if args.impl == "reference" else ola_arm(args)
     elif args.impl == "reference":
         reference_arm(args)
     elif args.workload == "serving":

@@ -43,8 +43,10 @@ struct OlaGeom {
 
 // One warp-tile: blocks tl B .. tl B + B - 1 of signal sig. prime: only leave the tails (the
 // warp's range starts inside the signal and the next tile needs its predecessor's tail).
-template <int N>
-__device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t tl, bool prime,
+// QOVL: the overlap is N/4, so D = N/8 is a whole number E/8 of register rows and every position
+// test below is a compile-time row test; otherwise positions are computed at run time.
+template <int N, bool QOVL>
+__device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t tl, bool prime, bool has_next,
                                          const float2* tw_s, unsigned char* wbase, int lane, int& table_key)
 {
     using G = OlsGeom<N>;
@@ -54,7 +56,7 @@ __device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t 
     float* gtab = reinterpret_cast<float*>(wbase + G::GAIN_OFF) + bsub * G::GT;
     unsigned char* slots = wbase + G::WARP_BYTES;
     const float4* twrow = reinterpret_cast<const float4*>(tw_s + t * G::TWROW);
-    const int O = a.O, M = N - O, D = O >> 1;
+    const int O = QOVL ? N / 4 : a.O, M = N - O, D = O >> 1;
 
     const int64_t blk = tl * B + bsub;
     const bool active = blk < a.nblocks;
@@ -66,14 +68,27 @@ __device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t 
     if (__all_sync(0xffffffffu, active && s0 + M <= a.nsamples)) {
         const float2* sp = in + s0 + t;
         static_for<0, E>([&](auto n1) {
-            constexpr int K = decltype(n1)::value * T;
-            x[n1] = (K + t < M) ? ld_stream(sp + K) : make_float2(0.f, 0.f);
+            constexpr int N1 = decltype(n1)::value;
+            constexpr int K = N1 * T;
+            if constexpr (QOVL) x[n1] = (N1 < 3 * E / 4) ? ld_stream(sp + K) : make_float2(0.f, 0.f);
+            else x[n1] = (K + t < M) ? ld_stream(sp + K) : make_float2(0.f, 0.f);
         });
     } else {
         static_for<0, E>([&](auto n1) {
             const int i = decltype(n1)::value * T + t;
             x[n1] = (active && i < M && s0 + i < a.nsamples) ? ld_stream(in + s0 + i) : make_float2(0.f, 0.f);
         });
+    }
+
+    // ---- ask L2 for the next tile's input span (B M samples after this tile's), one bulk
+    //      prefetch from a 16-byte aligned start
+    if (lane == 0 && has_next) {
+        int64_t e = (tl + 1) * (int64_t)B * M;
+        int64_t e2 = e + (int64_t)B * M;
+        if (e2 > a.nsamples) e2 = a.nsamples;
+        if ((reinterpret_cast<uintptr_t>(in + e) & 15) != 0) ++e;
+        const int64_t cnt = (e2 - e) & ~int64_t(1);
+        if (cnt > 0) prefetch_l2_bulk(in + e, (uint32_t)(cnt * sizeof(float2)));
     }
 
     // ---- gain table for this block's band (re-indexing only: eq. (FS_Hk_real))
@@ -108,46 +123,52 @@ __device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t 
     const int64_t bk = tl * B + bsub;
     const int slot = (SLOTS == 1) ? 0 : (int)(bk % SLOTS);
     float2* own = reinterpret_cast<float2*>(slots + (size_t)slot * a.slot_bytes);
+    // position of register row n1: n = (T n1 + t + D) mod N; for QOVL the row (n1 + E/8) mod E
     auto pos = [&](int n1) {
         int n = n1 * T + base;
         return n >= N ? n - N : n;
     };
+    // is_carry: n < O (the previous block's tail adds here); is_tail: n >= M (left for the next
+    // block at n - M); is_kept: n < M (stored)
+    auto body = [&](auto n1, auto&& on_carry, auto&& on_tail, auto&& on_kept) {
+        constexpr int N1 = decltype(n1)::value;
+        if constexpr (QOVL) {
+            constexpr int r = (N1 + E / 8) % E;
+            if constexpr (r < E / 4) on_carry(r * T + t);
+            if constexpr (r >= 3 * E / 4) on_tail((r - 3 * E / 4) * T + t);
+            if constexpr (r < 3 * E / 4) on_kept(r * T + t);
+        } else {
+            const int n = pos(N1);
+            if (n < O) on_carry(n);
+            if (n >= M) on_tail(n - M);
+            if (n < M) on_kept(n);
+        }
+    };
+    auto none = [](int) {};
+    auto leave_tail = [&](auto n1) {
+        body(n1, none, [&](int i) { own[i] = make_float2(x[n1].y, x[n1].x); }, none);
+    };
+    auto add_from = [&](const float2* src, auto n1) {
+        body(n1, [&](int i) {
+            const float2 c = src[i];
+            x[n1].y += c.x;
+            x[n1].x += c.y;
+        }, none, none);
+    };
     if constexpr (SLOTS == 1) {
         // add the previous block's tail z_{m-1}(n + M), n < O, in place; then leave this one's
-        if (!prime && bk > 0) {
-            static_for<0, E>([&](auto n1) {
-                const int n = pos(decltype(n1)::value);
-                if (n < O) {
-                    const float2 c = own[n];
-                    x[n1].y += c.x;
-                    x[n1].x += c.y;
-                }
-            });
-        }
+        if (!prime && bk > 0) static_for<0, E>([&](auto n1) { add_from(own, n1); });
         __syncwarp();
-        static_for<0, E>([&](auto n1) {
-            const int n = pos(decltype(n1)::value);
-            if (n >= M) own[n - M] = make_float2(x[n1].y, x[n1].x);
-        });
+        static_for<0, E>([&](auto n1) { leave_tail(n1); });
         __syncwarp();
     } else {
         // leave this block's tail, then add the predecessor's (slot (m - 1) mod (B + 1))
-        static_for<0, E>([&](auto n1) {
-            const int n = pos(decltype(n1)::value);
-            if (n >= M) own[n - M] = make_float2(x[n1].y, x[n1].x);
-        });
+        static_for<0, E>([&](auto n1) { leave_tail(n1); });
         __syncwarp();
         if (!prime && bk > 0) {
             const int ps = (int)((bk + SLOTS - 1) % SLOTS);
             const float2* prev = reinterpret_cast<const float2*>(slots + (size_t)ps * a.slot_bytes);
-            static_for<0, E>([&](auto n1) {
-                const int n = pos(decltype(n1)::value);
-                if (n < O) {
-                    const float2 c = prev[n];
-                    x[n1].y += c.x;
-                    x[n1].x += c.y;
-                }
-            });
+            static_for<0, E>([&](auto n1) { add_from(prev, n1); });
         }
         __syncwarp();
     }
@@ -157,13 +178,20 @@ __device__ __forceinline__ void ola_tile(const OlaArgs& a, int64_t sig, int64_t 
     const int64_t so = bk * (int64_t)M;
     float2* out = a.out + sig * a.nsamples + so;
     const int64_t lim = a.nsamples - so;
-    static_for<0, E>([&](auto n1) {
-        const int n = pos(decltype(n1)::value);
-        if (n < M && n < lim) st_stream(out + n, make_float2(x[n1].y, x[n1].x));
-    });
+    if (lim >= M) {
+        static_for<0, E>([&](auto n1) {
+            body(n1, none, none, [&](int n) { st_stream(out + n, make_float2(x[n1].y, x[n1].x)); });
+        });
+    } else {
+        static_for<0, E>([&](auto n1) {
+            body(n1, none, none, [&](int n) {
+                if (n < lim) st_stream(out + n, make_float2(x[n1].y, x[n1].x));
+            });
+        });
+    }
 }
 
-template <int N, int WARPS>
+template <int N, int WARPS, bool QOVL>
 __global__ void __launch_bounds__(WARPS * 32) ola_fp32_kernel(const OlaArgs a)
 {
     using G = OlsGeom<N>;
@@ -180,13 +208,17 @@ __global__ void __launch_bounds__(WARPS * 32) ola_fp32_kernel(const OlaArgs a)
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     if (tb >= te) return;
-    // (signal, tile within it) of the range's first tile; stepped without divisions below
+    // (signal, tile within it) of the range's first tile, stepped without divisions below; a
+    // range that starts inside a signal first runs the preceding tile for its tails only
     int64_t sig = tb / a.tiles_per_signal;
     int64_t tl = tb - sig * a.tiles_per_signal;
-    if (tl != 0) ola_tile<N>(a, sig, tl - 1, true, tw_s, wbase, lane, table_key);
+    int64_t tile = tb;
+    bool prime = tl != 0;
+    if (prime) { --tl; --tile; }
 #pragma unroll 1
-    for (int64_t tile = tb; tile < te; ++tile) {
-        ola_tile<N>(a, sig, tl, false, tw_s, wbase, lane, table_key);
+    for (; tile < te; ++tile) {
+        ola_tile<N, QOVL>(a, sig, tl, prime, tile + 1 < te, tw_s, wbase, lane, table_key);
+        prime = false;
         if (++tl == a.tiles_per_signal) { tl = 0; ++sig; }
     }
 }
@@ -200,7 +232,7 @@ cudaError_t launch_ola(const OlaArgs& a, int sms, cudaStream_t st)
     using G = OlsGeom<N>;
     const size_t smem = sizeof(float2) * G::TW + (size_t)WARPS * (G::WARP_BYTES +
                         (size_t)OlaGeom<N>::SLOTS * a.slot_bytes);
-    auto kern = ola_fp32_kernel<N, WARPS>;
+    auto kern = (a.O == N / 4) ? ola_fp32_kernel<N, WARPS, true> : ola_fp32_kernel<N, WARPS, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
