@@ -22,7 +22,8 @@
 //
 // Phasors e^{-j w x} (x a multiple of 1/2) come from the turn count (w / 4 pi) (2x) mod 1, split
 // into a 24-bit fixed-point part reduced exactly in integer arithmetic and a small float
-// remainder, then one sincospif per group of 16 taps. Inside a group the taps are summed against
+// remainder, then one sincospif per pair of 16-tap groups (the second group's seed is the first's
+// times e^{-j w 16}, one extra rounding). Inside a group the taps are summed against
 // a per-thread table e^{-j w l}, l < 16 (seeded the same way), and the group's seed multiplies the
 // group sum once: a tap costs two FMAs in the sums and, in the phase scan, one complex
 // multiply-add and a squared modulus. The running sums across groups are compensated (two-sum),
@@ -147,11 +148,19 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     float2 rot[kGroup];
 #pragma unroll
     for (int l = 0; l < kGroup; ++l) rot[l] = phasor(n1, g2, 2 * l);   // e^{-j w l}
+    const float2 rotg = phasor(n1, g2, 2 * kGroup);                      // e^{-j w 16}
+    // seed of the group starting at tap offset c0 (a = a0 + 2 c0): exact for even groups, the
+    // previous seed times e^{-j w 16} for odd ones
+    float2 seed = make_float2(1.f, 0.f);
+    auto group_seed = [&](int a0, int c0) {
+        seed = ((c0 / kGroup) & 1) ? cmulf(seed, rotg) : phasor(n1, g2, a0 + 2 * c0);
+        return seed;
+    };
 
     // R = sum_{q > O} a_q: a_q = h(q) e^{-j w (q - O/2)}, 2 (q - O/2) = O + 2 + 2 idx
     float Rx = 0.f, Ry = 0.f, Rcx = 0.f, Rcy = 0.f;
     for (int c0 = 0; c0 < pA; c0 += kGroup) {
-        const float2 base = phasor(n1, g2, O + 2 + 2 * c0);
+        const float2 base = group_seed(O + 2, c0);
         float qx = 0.f, qy = 0.f;
 #pragma unroll
         for (int l = 0; l < kGroup; ++l) {
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     // P0 = sum_{q <= O} a_q, 2 (q - O/2) = 2 q - O
     float Px = 0.f, Py = 0.f, Pcx = 0.f, Pcy = 0.f;
     for (int c0 = 0; c0 < pB; c0 += kGroup) {
-        const float2 base = phasor(n1, g2, 2 * c0 - O);
+        const float2 base = group_seed(-O, c0);
         float qx = 0.f, qy = 0.f;
 #pragma unroll
         for (int l = 0; l < kGroup; ++l) {
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(kPtThreads) ptvir_error_kernel(const PtArgs p)
     // the previous phase's value, which never replaces it (the first maximum is kept)
     float Ax = 0.f, Ay = 0.f, Acx = 0.f, Acy = 0.f;
     for (int c0 = 0; c0 < pA; c0 += kGroup) {
-        const float2 base = phasor(n1, g2, O + 2 + 2 * c0);
+        const float2 base = group_seed(O + 2, c0);
         const float2 A = make_float2(Ax + Acx, Ay + Acy);
         const float2 ac = make_float2(alpha.x + (u.x * A.x - u.y * A.y), alpha.y + (u.x * A.y + u.y * A.x));
         const float2 ub = cmulf(u, base);
