@@ -54,3 +54,31 @@ def test_stream_beyond_two_to_the_31_samples(cuda):
             tail, xs = xs[:O], xs[O:]
         ref = oracle.filter(N, O, V, 200, xs, tail=tail)
         assert_parity(y2[lo:hi].cpu().numpy(), ref, what=f"batch from {lo}")
+
+
+def test_overlap_add_beyond_two_to_the_31_samples(cuda):
+    """vbw_filter_ola on two signals of 2^30 + 333 samples each (2^31 + 666 in all, so the second
+    signal's samples sit past 32-bit indices of the back-to-back rows), against the OLA oracle on
+    sampled runs: each run starts one block early, since only the previous block's tail reaches
+    a block."""
+    torch = cuda
+    free, _ = torch.cuda.mem_get_info()
+    T = (1 << 30) + 333
+    if free < 2 * 8 * 2 * T + (4 << 30):
+        pytest.skip("needs about 38 GB of free device memory")
+    N, O = 1024, 256
+    M = N - O
+    V = wl.transition_table(12, 12)
+    plan = vbw.Plan(N, O, V)
+    g = torch.Generator(device="cuda").manual_seed(12)
+    x = torch.randn((2, T), dtype=torch.complex64, device="cuda", generator=g)
+    y = torch.zeros_like(x)
+    vbw.vbw_filter_ola(plan.handle, x, y, T, 2, 300)
+    torch.cuda.synchronize()
+    nb = (T + M - 1) // M
+    for c in range(2):
+        for b0 in (0, nb // 2, nb - 4):
+            lo = max(0, b0 - 1)
+            hi = min(T, (b0 + 4) * M)
+            ref = oracle.filter_ola(N, O, V, 300, x[c, lo * M:hi].cpu().numpy())
+            assert_parity(y[c, b0 * M:hi].cpu().numpy(), ref[(b0 - lo) * M:], what=f"signal {c} block {b0}")
