@@ -72,8 +72,9 @@ struct TcSmem {
     static constexpr size_t OFF_B1 = OFF_A + (size_t)P * A_PIECE;
     static constexpr size_t OFF_B2 = OFF_B1 + (size_t)P * B1_PIECE;
     static constexpr size_t OFF_T = OFF_B2 + (size_t)P * B2_PIECE;
-    static constexpr size_t OFF_TW = (OFF_T + sizeof(float) * T_FLOATS + 127) / 128 * 128;
-    static constexpr size_t OFF_V = OFF_TW + 2 * sizeof(float2) * N;   // W[a][b], then W[b][a]
+    // the twiddles W[a][b], W[b][a] stay in the plan's device table and are read through L1: the
+    // 2N float2 they would take here is what keeps a fifth CTA (N = 256) off the SM
+    static constexpr size_t OFF_V = (OFF_T + sizeof(float) * T_FLOATS + 127) / 128 * 128;
     static constexpr size_t OFF_BAR = (OFF_V + sizeof(float) * (N / 2) + 127) / 128 * 128;
     static constexpr size_t BYTES = OFF_BAR + 64;
     // per-plan device table: B1 pieces then B2 pieces (shared-memory image), then the twiddles
@@ -164,8 +165,8 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
     unsigned char* B1 = sm + G::OFF_B1;
     unsigned char* B2 = sm + G::OFF_B2;
     float* Tb = reinterpret_cast<float*>(sm + G::OFF_T);
-    const float2* twA = reinterpret_cast<const float2*>(sm + G::OFF_TW);   // [k1][n2]
-    const float2* twB = twA + N;                                           // [k1'][k1]
+    const float2* twA = reinterpret_cast<const float2*>(a.tc_tables + G::MAT_BYTES);   // [k1][n2]
+    const float2* twB = twA + N;                                                       // [k1'][k1]
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + 8);
@@ -175,9 +176,6 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
         const uint4* src = reinterpret_cast<const uint4*>(a.tc_tables);
         uint4* dst = reinterpret_cast<uint4*>(sm + G::OFF_B1);
         for (int i = tid; i < (int)(G::MAT_BYTES / 16); i += kTcThreads) dst[i] = src[i];
-        const float4* ts = reinterpret_cast<const float4*>(a.tc_tables + G::MAT_BYTES);
-        float4* td = reinterpret_cast<float4*>(sm + G::OFF_TW);
-        for (int i = tid; i < N; i += kTcThreads) td[i] = ts[i];
         for (int i = tid; i < a.LV; i += kTcThreads) Vs[i] = a.V[i];
     }
     if (tid == 0) {
@@ -301,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
                 if constexpr (K1 == 32) {
 #pragma unroll
                     for (int k1 = 0; k1 < R1; ++k1) {
-                        const float2 w = twA[k1 * R2 + n2];
+                        const float2 w = __ldg(twA + k1 * R2 + n2);
                         const float re = d[k1] * rs[0], im = d[R1 + k1] * rs[0];
                         float* row = Tb + (b * R1 + k1) * G::TROW1;
                         row[n2] = re * w.x - im * w.y;
@@ -317,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
                         if (c == 0) {
                             row[n2] = d[k1] * rs[0];
                         } else {
-                            const float2 w = twA[k1 * R2 + n2];
+                            const float2 w = __ldg(twA + k1 * R2 + n2);
                             const float re = row[n2], im = d[k1] * rs[0];
                             row[n2] = re * w.x - im * w.y;
                             row[R2 + n2] = re * w.y + im * w.x;
@@ -391,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
             tmem_ld32(lane_tmem + (uint32_t)(h * K2), d);
 #pragma unroll
             for (int kp = 0; kp < R2; ++kp) {
-                const float2 w = twB[kp * R1 + k1];
+                const float2 w = __ldg(twB + kp * R1 + k1);
                 const float re = d[kp] * rs[h], im = d[R2 + kp] * rs[h];
                 float* row = Tb + (b * R2 + kp) * G::TROW3;
                 row[k1] = re * w.x - im * w.y;
