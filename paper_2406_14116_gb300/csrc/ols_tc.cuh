@@ -68,20 +68,29 @@ struct TcSmem {
     static constexpr int TROW3 = 2 * R1 + 1;                       // transpose after round 3
     static constexpr int T_FLOATS = (kTcBlocks * R1 * TROW1 > kTcBlocks * R2 * TROW3)
                                         ? kTcBlocks * R1 * TROW1 : kTcBlocks * R2 * TROW3;
+    // ALIAS (one round-2 row per thread, N = 256): the transpose buffer shares the operand
+    // buffer. A transpose is written only after the previous round's MMAs completed (their
+    // operands are consumed), and every thread reads its transposed row into registers before
+    // any thread writes the next operands (a barrier in between).
+    static constexpr bool ALIAS = kTcBlocks * R1 == kTcThreads;
+    static constexpr size_t A_BYTES = (size_t)P * A_PIECE;
+    static constexpr size_t T_BYTES = sizeof(float) * T_FLOATS;
     static constexpr size_t OFF_A = 0;
-    static constexpr size_t OFF_B1 = OFF_A + (size_t)P * A_PIECE;
+    static constexpr size_t OFF_B1 =
+        ALIAS ? ((A_BYTES > T_BYTES ? A_BYTES : T_BYTES) + 127) / 128 * 128 : OFF_A + A_BYTES;
     static constexpr size_t OFF_B2 = OFF_B1 + (size_t)P * B1_PIECE;
-    static constexpr size_t OFF_T = OFF_B2 + (size_t)P * B2_PIECE;
-    // the twiddles W[a][b], W[b][a] stay in the plan's device table and are read through L1: the
-    // 2N float2 they would take here is what keeps a fifth CTA (N = 256) off the SM
-    static constexpr size_t OFF_V = (OFF_T + sizeof(float) * T_FLOATS + 127) / 128 * 128;
+    static constexpr size_t OFF_T = ALIAS ? OFF_A : OFF_B2 + (size_t)P * B2_PIECE;
+    static constexpr size_t OFF_END = ALIAS ? OFF_B2 + (size_t)P * B2_PIECE : OFF_T + T_BYTES;
+    // the twiddles W[a][b], W[b][a] stay in the plan's device table and are read through L1
+    static constexpr size_t OFF_V = (OFF_END + 127) / 128 * 128;
     static constexpr size_t OFF_BAR = (OFF_V + sizeof(float) * (N / 2) + 127) / 128 * 128;
     static constexpr size_t BYTES = OFF_BAR + 64;
     // per-plan device table: B1 pieces then B2 pieces (shared-memory image), then the twiddles
-    static constexpr size_t MAT_BYTES = OFF_T - OFF_B1;
+    static constexpr size_t MAT_BYTES = (size_t)P * (B1_PIECE + B2_PIECE);
     static constexpr size_t TABLE_BYTES = MAT_BYTES + 2 * sizeof(float2) * N;
     static_assert(OFF_B1 % 128 == 0 && OFF_B2 % 128 == 0 && OFF_T % 16 == 0, "alignment");
     static_assert(MAT_BYTES % 16 == 0, "16-byte copies");
+    static_assert(MAT_BYTES == OFF_B2 + (size_t)P * B2_PIECE - OFF_B1, "matrix image is contiguous");
 };
 
 // Power-of-two scale of a data row for the FP16 variant: v * inv lies in (-1, 1), v = (v * inv) * s.
@@ -342,6 +351,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
             float inv = 1.f;
             rs[h] = 1.f;
             if constexpr (S::SCALED) row_scale(mx, rs[h], inv);
+            if constexpr (G::ALIAS) __syncthreads();   // every transposed row read before overwriting
             put_row<PREC, K2>(Abuf, G::A_PIECE, r, v, inv);
         }
         if (!(alive = round(std::integral_constant<int, K2>{}, B2, G::B2_PIECE, H2))) break;
@@ -412,6 +422,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
             float inv = 1.f;
             rs[0] = 1.f;
             if constexpr (S::SCALED) row_scale(mx, rs[0], inv);
+            if constexpr (G::ALIAS) __syncthreads();   // every transposed row read before overwriting
             put_row<PREC, K1>(Abuf, G::A_PIECE, tid, v, inv);
         }
         if (!(alive = round(std::integral_constant<int, K1>{}, B1, G::B1_PIECE, 1))) break;
