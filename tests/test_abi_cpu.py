@@ -59,7 +59,9 @@ def test_plan_rejects_unknown_precision(L):
 def test_null_handles_are_rejected(L):
     for f, args in ((L.vbw_filter, (None, None, None, 1)), (L.vbw_set_bandwidth, (None, 3)),
                     (L.vbw_stream_reset, (None, 3)), (L.vbw_batch_run, (None, None)),
-                    (L.vbw_plan_destroy, (None,)), (L.vbw_stream_destroy, (None,))):
+                    (L.vbw_plan_destroy, (None,)), (L.vbw_stream_destroy, (None,)),
+                    (L.vbw_filter_ola, (None, None, None, 100, 1, 5, None, None)),
+                    (L.vbw_ptvir_error, (None, None, 1, None, None, 10, None, None, None))):
         assert f(*args) == 1
         assert vbw.vbw_last_error()
 
