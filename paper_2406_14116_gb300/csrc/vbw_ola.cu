@@ -17,6 +17,10 @@
 //     warp barrier each adds its predecessor's (the previous lane group's, or for the first lane
 //     group the previous tile's last one, whose slot this tile does not reuse).
 // A warp whose range starts inside a signal first runs the preceding tile for its tails only.
+// Each tile also asks L2 for the next tile's input span (one bulk prefetch), as the OLS kernel does.
+// For overlap N/4 (every workload's geometry) D = N/8 is a whole number of register rows, so the
+// position of every register and the carry / tail / store tests are compile-time; other even
+// overlaps compute them at run time.
 // Nothing is stored per band: the gains come from (k1, V) through the per-lane-group table.
 #include "ols_fp32.cuh"
 #include "vbw_internal.h"
