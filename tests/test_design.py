@@ -91,3 +91,20 @@ def test_candidate_rows_equal_the_full_responses():
         A, c = design.candidate_rows(N, L, LV, np.full(20, k1), n, w[i], d[i])
         np.testing.assert_allclose(A, F[n, i, 1:], atol=1e-14)
         np.testing.assert_allclose(c, F[n, i, 0] - d[i], atol=1e-14)
+
+
+def test_candidate_rows_match_the_oracle_ptvir_errors():
+    """|A V + c| at (band, phase, frequency) points equals the oracle's PTVIR error there
+    (eq. (OLS_Hn), eq. (err_min), from the OLS definition), for float32-exact V."""
+    N, L, LV = 64, 17, 5
+    O = L - 1
+    g = np.random.default_rng(9)
+    V = np.sort(g.uniform(0, 1, LV))[::-1].astype(np.float32).astype(np.float64)
+    for k1 in (2, 9, 64 // 2 - LV - 1):
+        w = g.uniform(0, np.pi, 9)
+        d = (g.uniform(0, 1, 9) < 0.5).astype(float)
+        E = oracle.ptvir_errors(N, O, V, k1, w, d)                      # (M, K)
+        n = g.integers(0, N - O, 25)
+        i = g.integers(0, 9, 25)
+        A, c = design.candidate_rows(N, L, LV, np.full(25, k1), n, w[i], d[i])
+        np.testing.assert_allclose(np.abs(A @ V + c), E[n, i], atol=1e-12)
