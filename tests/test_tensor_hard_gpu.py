@@ -1,0 +1,168 @@
+"""The tensor-core split precisions on inputs where 16-bit operand pieces can fail, against the
+FP64 oracle, beside the FP32 path on the same input (through the C ABI).
+
+Input classes (N = 256 and 512, overlap N/4, every split variant):
+  * wide dynamic range between blocks: runs of blocks whose amplitudes differ by 1e6 inside one
+    8-block tensor-core tile. Every block whose whole input span is small must keep the relative
+    accuracy of a unit-level block (the FP16 variant rescales each GEMM row by a power of two;
+    without it those rows would underflow).
+  * wide dynamic range inside one GEMM row: samples x(16 n1 + n2) of a round-1 row alternate
+    between amplitude 1 and 1e-6 with n1.
+  * a strong stopband tone: a bin-centred tone of amplitude 1e3 in the stopband beside unit
+    white noise. The filter removes the tone exactly (H_R = 0 there), so the output carries
+    about 1e-6 of the input energy. Every floating-point transform, the FP32 one included, makes
+    errors in proportion to the input's energy, spread over all bins; here the gate is therefore
+    applied to the error relative to the input RMS (the output-relative error is reported).
+  * the mixed workload's signal: unit noise plus 1-8 tones (amplitude 0.5-2, random frequency),
+    under the output-relative gates.
+The gates: RMS error <= 1e-5 for every split, <= 2e-6 for FP32 (the parity gates).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import FP32_RMS_TOL, rms_rel
+from paper_2406_14116_gb300 import vbw
+from paper_2406_14116_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SPLITS = {"bf16x3": vbw.VBW_PREC_BF16_SPLIT, "fp16s": vbw.VBW_PREC_FP16_SCALED,
+          "bf16x6": vbw.VBW_PREC_BF16_SPLIT3}
+ALL = dict(SPLITS, fp32=vbw.VBW_PREC_FP32)
+TOL = {"bf16x3": 1e-5, "fp16s": 1e-5, "bf16x6": 1e-5, "fp32": FP32_RMS_TOL}
+LV = 12
+
+
+def run_batch(torch, plan, x, bands):
+    """One signal through a prepared batch (the launch path bench.py times)."""
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    b = vbw.Batch([(plan, xd, yd, bands)])
+    b.run()
+    torch.cuda.synchronize()
+    b.close()
+    return yd.cpu().numpy()
+
+
+def filtered(torch, N, prec, V, bands, x):
+    plan = vbw.Plan(N, N // 4, V, precision=ALL[prec])
+    try:
+        return run_batch(torch, plan, x, bands)
+    finally:
+        plan.close()
+
+
+def report(tag, **kv):
+    print("REPORT", tag, " ".join(f"{k}={v:.3e}" if isinstance(v, float) else f"{k}={v}"
+                                  for k, v in kv.items()))
+
+
+@pytest.mark.parametrize("N", [256, 512])
+@pytest.mark.parametrize("prec", list(ALL))
+def test_block_amplitudes_1e6_apart(cuda, N, prec):
+    """Blocks of amplitude 1e3 and 1e-3 in the pattern L, S, S, L, S, S, ... (one tile holds
+    both). Blocks whose input span lies entirely in small blocks are checked on their own."""
+    torch = cuda
+    O = N // 4
+    M = N - O
+    nb = 240
+    V = wl.transition_table(900 + N, LV)
+    k1 = N // 8
+    x = wl.complex_gaussian(901, N, nb * M).astype(np.complex128)
+    amp = np.where(np.arange(nb) % 3 == 0, 1e3, 1e-3)
+    x = (x * np.repeat(amp, M)).astype(np.complex64)
+    bands = np.full(nb, k1, np.int32)
+    y = filtered(torch, N, prec, V, bands, x)
+    ref = oracle.filter(N, O, V, bands, x)
+    assert np.isfinite(y).all()
+    whole = rms_rel(y, ref)
+    # block m reads x(mM - O .. mM + M - 1): all small when blocks m - 1 and m are small
+    small = [m for m in range(1, nb) if amp[m] < 1 and amp[m - 1] < 1]
+    idx = np.concatenate([np.arange(m * M, (m + 1) * M) for m in small])
+    small_err = rms_rel(y[idx], ref[idx])
+    report(f"block_range N={N} {prec}", whole=whole, small_blocks=small_err)
+    assert whole <= TOL[prec], (whole, TOL[prec])
+    assert small_err <= TOL[prec], (small_err, TOL[prec])
+
+
+@pytest.mark.parametrize("N", [256, 512])
+@pytest.mark.parametrize("prec", list(ALL))
+def test_row_amplitudes_1e6_apart(cuda, N, prec):
+    """Inside every round-1 GEMM row x(16 n1 + n2), n1 < R1, the samples alternate between unit
+    amplitude and 1e-6 with n1."""
+    torch = cuda
+    O = N // 4
+    M = N - O
+    nb = 160
+    V = wl.transition_table(910 + N, LV)
+    g = np.random.default_rng(911 + N)
+    bands = np.repeat(g.integers(1, wl.max_band(N, LV) + 1, nb // 16 + 1), 16)[:nb].astype(np.int32)
+    n = nb * M + M // 2
+    x = wl.complex_gaussian(912, N, n).astype(np.complex128)
+    # block m starts at sample mM - O, a multiple of 16, so (s // 16) % 2 is n1 % 2 in every row
+    s = np.arange(n)
+    x = (x * np.where((s // 16) % 2 == 0, 1.0, 1e-6)).astype(np.complex64)
+    bands = np.concatenate([bands, bands[-1:]])
+    y = filtered(torch, N, prec, V, bands, x)
+    ref = oracle.filter(N, O, V, bands, x)
+    err = rms_rel(y, ref)
+    report(f"row_range N={N} {prec}", err=err)
+    assert np.isfinite(y).all()
+    assert err <= TOL[prec], (err, TOL[prec])
+
+
+@pytest.mark.parametrize("N", [256, 512])
+@pytest.mark.parametrize("prec", list(ALL))
+def test_strong_stopband_tone(cuda, N, prec):
+    """A bin-centred stopband tone of amplitude 1e3 beside unit white noise: the error relative
+    to the input RMS meets the gate; the output-relative error is reported."""
+    torch = cuda
+    O = N // 4
+    M = N - O
+    nb = 200
+    V = wl.transition_table(920 + N, LV)
+    k1 = N // 16
+    ks = N // 2 - 5                       # inside the stopband [k1 + L_V, N - k1 - L_V]
+    assert ks > k1 + LV - 1
+    n = nb * M
+    t = np.arange(n)
+    noise = wl.complex_gaussian(921, N, n).astype(np.complex128)
+    x = (noise + 1e3 * np.exp(2j * np.pi * ks * t / N)).astype(np.complex64)
+    bands = np.full(nb, k1, np.int32)
+    y = filtered(torch, N, prec, V, bands, x)
+    ref = oracle.filter(N, O, V, bands, x)
+    assert np.isfinite(y).all()
+    out_rel = rms_rel(y, ref)
+    err = np.sqrt(np.mean(np.abs(y.astype(np.complex128) - ref) ** 2))
+    in_rel = float(err / np.sqrt(np.mean(np.abs(x.astype(np.complex128)) ** 2)))
+    # the oracle removes the tone: its output is the filtered noise up to the complex64
+    # rounding of the sum noise + tone (about 6e-8 of 1e3 per sample)
+    noise_only = oracle.filter(N, O, V, bands, noise.astype(np.complex64))
+    assert rms_rel(ref, noise_only) < 1e-3
+    report(f"stopband_tone N={N} {prec}", input_rel=in_rel, output_rel=out_rel)
+    assert in_rel <= TOL[prec], (in_rel, TOL[prec])
+
+
+@pytest.mark.parametrize("N", [256, 512])
+@pytest.mark.parametrize("prec", list(ALL))
+def test_tones_signal(cuda, N, prec):
+    """The mixed workload's noise-plus-tones signal on six streams with random bands, under the
+    output-relative gates."""
+    torch = cuda
+    O = N // 4
+    M = N - O
+    V = wl.transition_table(930 + N, LV)
+    g = np.random.default_rng(931 + N)
+    worst = 0.0
+    for sid in range(6):
+        n = int(g.integers(60, 200)) * M + int(g.integers(0, M))
+        x = wl.tones_signal(3, 50_000 + 10 * N + sid, n)
+        nbk = wl.nblocks_for(n, N, O)
+        bands = np.full(nbk, int(g.integers(1, wl.max_band(N, LV) + 1)), np.int32)
+        y = filtered(torch, N, prec, V, bands, x)
+        ref = oracle.filter(N, O, V, bands, x)
+        assert np.isfinite(y).all()
+        worst = max(worst, rms_rel(y, ref))
+    report(f"tones N={N} {prec}", worst=worst)
+    assert worst <= TOL[prec], (worst, TOL[prec])
