@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import concurrent.futures as cf
 import ctypes
+import gc
 import hashlib
 import json
 import math
@@ -828,7 +829,16 @@ def serving_run(args):
     run(open_loop=False, limit=min(nreq, 4000))     # warm-up: first launches, page-in
     sampler = ClockSampler(device_uuid(torch, local))
     sampler.start()
-    sched, done_t, t0, t_end, info = run(open_loop=True)
+    # no garbage-collector pauses inside the arrival loop (a serving process keeps its heap
+    # frozen while it serves)
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        sched, done_t, t0, t_end, info = run(open_loop=True)
+    finally:
+        gc.enable()
+        gc.unfreeze()
     clocks = sampler.stop()
     lat = (done_t - sched) * 1e3
     samples = int(lens.sum())
@@ -952,7 +962,7 @@ def config_records(args):
         torch.cuda.empty_cache()
 
         # serving: 2000 streams, Poisson arrivals at 50k chunks/s for a few seconds, then saturation
-        a = sub(workload="serving", duration=3.0)
+        a = sub(workload="serving", duration=5.0)
         line = serving_run(a)
         out["serving"] = {
             "workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],

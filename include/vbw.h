@@ -211,10 +211,12 @@ vbw_status vbw_plan_status(vbw_plan_t plan, int* flags, int clear);
 vbw_status vbw_debug_set(int flags);
 
 /* Test hook: D (128 x NN) = A (128 x K) B (K x NN) on the tensor cores through the operand
- * layout, descriptors, TMEM accumulator and waits the tensor-core OLS kernel uses, with A and B
- * rounded once to bfloat16 (bf16 != 0) or float16. K, NN in {32, 64}; host float arrays,
- * row-major. Synchronous; allocates. */
-vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A, const float* B, float* D);
+ * layouts, descriptors, TMEM accumulator and waits the tensor-core OLS kernel uses, with A and B
+ * rounded once to 16 bits. flags: bit 0 set = bfloat16, clear = float16; bit 1 set = A stored in
+ * MN-major core matrices (the layout of rounds 2 and 4), clear = K-major; bit 2 (with bit 1) =
+ * the A descriptor's leading and stride byte offsets exchanged. K, NN in {32, 64}; host float
+ * arrays, row-major. Synchronous; allocates. */
+vbw_status vbw_debug_tc_gemm(int flags, int K, int NN, const float* A, const float* B, float* D);
 
 /* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
  * produced by the same device code and register layout, to host_out (N floats). Synchronous. */

@@ -79,7 +79,7 @@ size_t tc_table_bytes(int N, int prec)
 
 cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st)
 {
-    const int n = 2 * (2 * 32) * (2 * 32) + 2048;   // covers matrix entries and twiddles
+    const int n = (2 * 32) * (2 * 32) + 2 * (2 * 16) * (2 * 16) + 2048;   // covers matrix entries and twiddles
 #define VBW_TC_TAB(NN, PP)                                                                      \
     if (N == NN && prec == PP) {                                                                \
         tc_table_kernel<NN, PP><<<(n + 255) / 256, 256, 0, st>>>(out);                          \
@@ -97,9 +97,11 @@ cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st)
 
 // ---- GEMM test: D (128 x NN) = A (128 x K) B (K x NN) with one rounding of A and B to 16 bits,
 // through the same descriptors, instruction descriptor, TMEM load and waits the OLS kernel uses.
+// flags: bit 0 BF16 (else FP16); bit 1 A in MN-major core matrices (as rounds 2 and 4 of the OLS
+// kernel take it), else K-major; bit 2 (with bit 1) the A descriptor's two byte offsets exchanged.
 template <bool BF16>
 __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const float* B, float* D, int K,
-                                                             int NN, int* status)
+                                                             int NN, int flags, int* status)
 {
     using H = Half16<BF16>;
     using T16 = typename H::T;
@@ -109,8 +111,11 @@ __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 128 * 64 * 2 + 64 * 64 * 2);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    for (int k = 0; k < K; ++k)
-        *reinterpret_cast<T16*>(As + core_offset(tid, k, K)) = H::from(A[tid * K + k]);
+    const bool a_mn = (flags & 2) != 0;
+    for (int k = 0; k < K; ++k) {
+        const uint32_t off = a_mn ? mn_line_offset(tid & ~7, k, K) + (tid & 7) * 2 : core_offset(tid, k, K);
+        *reinterpret_cast<T16*>(As + off) = H::from(A[tid * K + k]);
+    }
     if (tid < NN)
         for (int k = 0; k < K; ++k)
             *reinterpret_cast<T16*>(Bs + core_offset(tid, k, K)) = H::from(B[k * NN + tid]);
@@ -128,11 +133,12 @@ __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const
     tc_fence_after_sync();
     const uint32_t tmem = *tslot;
     if (tid == 0) {
-        const uint32_t idesc = umma_idesc(BF16, 128, NN);
+        const uint32_t idesc = umma_idesc(BF16, 128, NN) | (a_mn ? (1u << 15) : 0u);
         const uint32_t sbo = (uint32_t)(K / 8) * 128;
+        const bool swap = a_mn && (flags & 4);
         for (int s = 0; s < K / 16; ++s)
-            umma_f16(tmem, umma_desc(As + s * 256, 128, sbo), umma_desc(Bs + s * 256, 128, sbo), idesc,
-                     s > 0 ? 1u : 0u);
+            umma_f16(tmem, umma_desc(As + s * 256, swap ? sbo : 128, swap ? 128 : sbo),
+                     umma_desc(Bs + s * 256, 128, sbo), idesc, s > 0 ? 1u : 0u);
         umma_commit(bar);
     }
     bool ok = mbar_wait_bounded(bar, 0, kWaitLimitCycles);
@@ -158,7 +164,7 @@ namespace vbw {
 vbw_status set_error(vbw_status st, const char* msg);
 }
 
-extern "C" vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A, const float* B, float* D)
+extern "C" vbw_status vbw_debug_tc_gemm(int flags, int K, int NN, const float* A, const float* B, float* D)
 {
     using namespace vbw;
     if ((K != 32 && K != 64) || (NN != 32 && NN != 64) || !A || !B || !D)
@@ -174,12 +180,12 @@ extern "C" vbw_status vbw_debug_tc_gemm(int bf16, int K, int NN, const float* A,
     if (e == cudaSuccess) e = cudaMemcpy(dB, B, sizeof(float) * K * NN, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(dS, 0, sizeof(int));
     if (e == cudaSuccess) {
-        if (bf16) {
+        if (flags & 1) {
             e = cudaFuncSetAttribute(tc_gemm_test_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) tc_gemm_test_kernel<true><<<1, 128, smem>>>(dA, dB, dD, K, NN, dS);
+            if (e == cudaSuccess) tc_gemm_test_kernel<true><<<1, 128, smem>>>(dA, dB, dD, K, NN, flags, dS);
         } else {
             e = cudaFuncSetAttribute(tc_gemm_test_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) tc_gemm_test_kernel<false><<<1, 128, smem>>>(dA, dB, dD, K, NN, dS);
+            if (e == cudaSuccess) tc_gemm_test_kernel<false><<<1, 128, smem>>>(dA, dB, dD, K, NN, flags, dS);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
     }

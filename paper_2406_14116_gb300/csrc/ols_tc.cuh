@@ -1,26 +1,40 @@
 // OLS VBW filtering with the DFT and IDFT stages as complex DFT-matrix GEMMs on the tensor cores
 // (tcgen05, FP32 accumulation in TMEM): the precision variant of the fused FP32 kernel.
 //
-// Four-step DFT with N = R1 * R2, on a tile of 8 consecutive blocks of one stream:
+// Four-step DFT with N = R1 * R2 (R2 = 16), on a tile of 8 consecutive blocks of one stream:
 //   round 1  rows (b, n2), n2 < R2: DFT-R1 of x_b(R2 n1 + n2) over n1   -> A1(k1), k1 < R1
-//            twiddle W_N^{n2 k1}, transpose through shared memory (FP32)
+//            twiddle W_N^{n2 k1} (FP32)
 //   round 2  rows (b, k1), k1 < R1: DFT-R2 over n2                      -> X_b(k1 + R1 k2)
 //            gains H_R(k)/N of eq. (FS_Hk_real), then swap(a + jb) = b + ja
 //   round 3  rows (b, k1): DFT-R2 over k2                                -> A'(k1'), k1' < R2
-//            twiddle W_N^{k1 k1'}, transpose
+//            twiddle W_N^{k1 k1'}
 //   round 4  rows (b, k1'): DFT-R1 over k1                               -> Z(k1' + R2 k2')
 // Rounds 3-4 are the forward four-step of size R2 x R1 applied to swap(H_R X / N); since
 // IDFT(y) = swap(DFT(swap(y))), z = swap(Z) is the IDFT of eq. (OLS_dn). The linear phase of
 // eq. (FS_Hk_exp) is the store shift by D = O/2, as in the FP32 kernel.
 //
-// Each round is D[row, :] = A[row, :] B with the DFT-R matrix in real form (K = N_out = 2R):
-// out = [yr; yi] = [[Fr, -Fi], [Fi, Fr]] [xr; xi]; B is stored K-major, i.e. as those rows.
-// Operands are 16-bit pieces in shared memory:
+// Each round is D[row, :] = A[row, :] B with the DFT-R matrix in real form: for out = [yr; yi],
+// in = [xr; xi], B = [[Fr, -Fi], [Fi, Fr]], stored K-major (one row per output). Operands are
+// 16-bit pieces in shared memory:
 //   BF16x3  v ~ hi + lo (bfloat16), products hi*hi + hi*lo + lo*hi          (3 MMAs per K step)
 //   BF16x6  v ~ hi + mid + lo, products hh hm mh hl lh mm                   (6 MMAs per K step)
-//   FP16S   each data row scaled into (-1, 1) by a power of two, hi + lo in fp16, products
-//           hi*hi + hi*lo + lo*hi; the accumulator row is scaled back exactly.
+//   FP16S   each block's operand values scaled into (-1, 1) by one power of two per block and
+//           round, hi + lo in fp16, products hi*hi + hi*lo + lo*hi; the accumulator rows are scaled
+//           back exactly.
 // The DFT matrices are generated in FP64 at plan time and split into the pieces there.
+//
+// No transposes: a round's epilogue thread holds one row of the accumulator, i.e. one column of
+// the next round's operand for 16 or 32 consecutive operand rows. Rounds 2 and 4 therefore take
+// their A operand in MN-major layout (8 consecutive rows of one column per 16-byte line), which the
+// epilogue writes with 128-bit stores straight from registers; rounds 1 and 3 take K-major rows.
+//
+// Stopband pruning (Sec. III-D: the bins where H_R = 0 cost nothing). The outputs of round 2 and the
+// inputs of round 3 are ordered so that the first 16 real slots hold the 8 bins k2 nearest 0 (mod
+// R2) and the last 16 slots the 8 inner bins k2 in [4, R2 - 5]. Those inner bins cover
+// k in [N/4, 3N/4 - 1], inside the stopband [k2b + 1, N - k2b - 1] whenever k2b = k1 + L_V - 1 <=
+// N/4 - 1. When every block of a tile has such a band, round 2 computes only the outer 16 output
+// columns and round 3 reads only the outer 16 inputs: half of both rounds' tensor work and of the
+// gain / split / store work between them is skipped.
 #pragma once
 
 #include "ols_fp32.cuh"
@@ -56,45 +70,55 @@ constexpr int kTcBlocks = 8;     // blocks per tile
 constexpr int kTcThreads = 128;  // one warpgroup
 constexpr int kTcTmemCols = 64;
 
+// Real slot s (0..31) of the round-2 outputs and round-3 inputs: bin k2 and part (0 re, 1 im).
+// Slots 0-7 re and 8-15 im of the outer bins {0, 1, 2, 3, 12, 13, 14, 15}; slots 16-23 re and
+// 24-31 im of the inner bins {4 .. 11}.
+__host__ __device__ constexpr int tc_slot_bin(int s)
+{
+    return (s >> 4) == 0 ? ((s & 7) < 4 ? (s & 7) : (s & 7) + 8) : (s & 7) + 4;
+}
+__host__ __device__ constexpr int tc_slot_part(int s) { return (s >> 3) & 1; }
+
+// Byte offset of 16-bit element (row, k) of an R x K operand in K-major core matrices (a core
+// matrix is 8 rows x 16 bytes along K), and of the 16-byte line holding rows row0 .. row0 + 7 of
+// column k in MN-major core matrices (8 K-lines x 16 bytes along the rows). Both use the same grid:
+// 128 bytes between core matrices along K, K/8 * 128 bytes between them along the rows.
+__host__ __device__ constexpr uint32_t mn_line_offset(int row0, int k, int K)
+{
+    return (uint32_t)(((row0 >> 3) * (K >> 3) + (k >> 3)) * 128 + (k & 7) * 16);
+}
+
 // Shared-memory plan of one CTA (bytes).
 template <int N, int PREC>
 struct TcSmem {
     static constexpr int R1 = TcGeom<N>::R1, R2 = TcGeom<N>::R2;
+    static_assert(R2 == 16, "the slot order of rounds 2-3 assumes R2 = 16");
     static constexpr int P = TcSplit<PREC>::PIECES;
     static constexpr int A_PIECE = kTcBlocks * N * 2 * 2;          // rows x K = 16 N in every round
     static constexpr int B1_PIECE = (2 * R1) * (2 * R1) * 2;       // DFT-R1 matrix, one piece
-    static constexpr int B2_PIECE = (2 * R2) * (2 * R2) * 2;       // DFT-R2 matrix, one piece
-    static constexpr int TROW1 = 2 * R2 + 1;                       // transpose after round 1
-    static constexpr int TROW3 = 2 * R1 + 1;                       // transpose after round 3
-    static constexpr int T_FLOATS = (kTcBlocks * R1 * TROW1 > kTcBlocks * R2 * TROW3)
-                                        ? kTcBlocks * R1 * TROW1 : kTcBlocks * R2 * TROW3;
-    // ALIAS (one round-2 row per thread, N = 256): the transpose buffer shares the operand
-    // buffer. A transpose is written only after the previous round's MMAs completed (their
-    // operands are consumed), and every thread reads its transposed row into registers before
-    // any thread writes the next operands (a barrier in between).
-    static constexpr bool ALIAS = kTcBlocks * R1 == kTcThreads;
-    static constexpr size_t A_BYTES = (size_t)P * A_PIECE;
-    static constexpr size_t T_BYTES = sizeof(float) * T_FLOATS;
+    static constexpr int B2_PIECE = (2 * R2) * (2 * R2) * 2;       // DFT-R2 matrices, one piece each
+    // per-block gain table g(kk) = H_R / N, kk = 0..N/2; the stride is 16 banks mod 32 so that two
+    // blocks read by one warp use disjoint banks
+    static constexpr int GT = ((N / 2 + 1 + 31) / 32) * 32 + 16;
     static constexpr size_t OFF_A = 0;
-    static constexpr size_t OFF_B1 =
-        ALIAS ? ((A_BYTES > T_BYTES ? A_BYTES : T_BYTES) + 127) / 128 * 128 : OFF_A + A_BYTES;
-    static constexpr size_t OFF_B2 = OFF_B1 + (size_t)P * B1_PIECE;
-    static constexpr size_t OFF_T = ALIAS ? OFF_A : OFF_B2 + (size_t)P * B2_PIECE;
-    static constexpr size_t OFF_END = ALIAS ? OFF_B2 + (size_t)P * B2_PIECE : OFF_T + T_BYTES;
-    // the twiddles W[a][b], W[b][a] stay in the plan's device table and are read through L1
-    static constexpr size_t OFF_V = (OFF_END + 127) / 128 * 128;
-    static constexpr size_t OFF_BAR = (OFF_V + sizeof(float) * (N / 2) + 127) / 128 * 128;
-    static constexpr size_t BYTES = OFF_BAR + 64;
-    // per-plan device table: B1 pieces then B2 pieces (shared-memory image), then the twiddles
-    static constexpr size_t MAT_BYTES = (size_t)P * (B1_PIECE + B2_PIECE);
+    static constexpr size_t OFF_B1 = OFF_A + (size_t)P * A_PIECE;
+    static constexpr size_t OFF_B2 = OFF_B1 + (size_t)P * B1_PIECE;    // round 2: slot-ordered outputs
+    static constexpr size_t OFF_B3 = OFF_B2 + (size_t)P * B2_PIECE;    // round 3: slot-ordered inputs
+    static constexpr size_t OFF_G = OFF_B3 + (size_t)P * B2_PIECE;
+    static constexpr size_t OFF_V = OFF_G + sizeof(float) * kTcBlocks * GT;
+    static constexpr size_t OFF_SC = OFF_V + sizeof(float) * (N / 2);  // FP16: block scales of A2, A4
+    static constexpr size_t OFF_BAR = OFF_SC + sizeof(float) * 2 * kTcBlocks;
+    static constexpr size_t BYTES = OFF_BAR + 16;
+    // per-plan device table: the B1, B2, B3 pieces (shared-memory image), then the FP32 twiddles
+    // W_N^{n2 k1} as [n2 < R2][k1 < R1] and W_N^{k1 k1'} as [k1 < R1][k1' < R2]
+    static constexpr size_t MAT_BYTES = (size_t)P * (B1_PIECE + 2 * B2_PIECE);
     static constexpr size_t TABLE_BYTES = MAT_BYTES + 2 * sizeof(float2) * N;
-    static_assert(OFF_B1 % 128 == 0 && OFF_B2 % 128 == 0 && OFF_T % 16 == 0, "alignment");
-    static_assert(MAT_BYTES % 16 == 0, "16-byte copies");
-    static_assert(MAT_BYTES == OFF_B2 + (size_t)P * B2_PIECE - OFF_B1, "matrix image is contiguous");
+    static_assert(OFF_B1 % 128 == 0 && OFF_B2 % 128 == 0 && OFF_B3 % 128 == 0 && OFF_G % 16 == 0, "alignment");
+    static_assert(MAT_BYTES % 16 == 0 && OFF_BAR % 8 == 0, "16-byte copies, mbarrier alignment");
 };
 
-// Power-of-two scale of a data row for the FP16 variant: v * inv lies in (-1, 1), v = (v * inv) * s.
-__device__ __forceinline__ void row_scale(float maxabs, float& s, float& inv)
+// Power-of-two scale for the FP16 variant: v * inv lies in (-1, 1), v = (v * inv) * s.
+__device__ __forceinline__ void pow2_scale(float maxabs, float& s, float& inv)
 {
     const uint32_t E = (__float_as_uint(maxabs) >> 23) & 0xFFu;
     if (E == 0 || E >= 250) {
@@ -107,78 +131,151 @@ __device__ __forceinline__ void row_scale(float maxabs, float& s, float& inv)
     inv = __uint_as_float((uint32_t)(127 - e) << 23);
 }
 
-// Writes row `row` (K real values v, times inv) of the 16-bit operand pieces in core-matrix layout.
-template <int PREC, int K>
-__device__ __forceinline__ void put_row(unsigned char* A, size_t piece_bytes, int row, const float* v, float inv)
+// Maximum over the LANES consecutive lanes (a power of two <= 32) that hold one block.
+template <int LANES>
+__device__ __forceinline__ float lane_group_max(float m)
+{
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
+// (v0, v1) -> one 32-bit word per piece, element v0 in the low half (the lower address).
+template <int PREC>
+__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t (&w)[TcSplit<PREC>::PIECES])
 {
     using S = TcSplit<PREC>;
-    using H = Half16<S::BF16>;
-    using T16 = typename H::T;
-    constexpr int P = S::PIECES;
-#pragma unroll
-    for (int c = 0; c < K / 8; ++c) {
-        T16 pc[P][8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            float r = v[c * 8 + e] * inv;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const T16 q = H::from(r);
-                pc[p][e] = q;
-                r -= H::to(q);
-            }
+    if constexpr (S::BF16) {
+        uint32_t h;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(v1), "f"(v0));
+        w[0] = h;
+        float r0 = v0 - __uint_as_float(h << 16), r1 = v1 - __uint_as_float(h & 0xFFFF0000u);
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(r1), "f"(r0));
+        w[1] = h;
+        if constexpr (S::PIECES == 3) {
+            r0 -= __uint_as_float(h << 16);
+            r1 -= __uint_as_float(h & 0xFFFF0000u);
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(r1), "f"(r0));
+            w[2] = h;
         }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            uint4 w;
-            memcpy(&w, pc[p], 16);
-            *reinterpret_cast<uint4*>(A + (size_t)p * piece_bytes + core_offset(row, c * 8, K)) = w;
-        }
+    } else {
+        uint32_t h;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(v1), "f"(v0));
+        w[0] = h;
+        float f0, f1;
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
+            : "=f"(f0), "=f"(f1) : "r"(h));
+        const float r0 = v0 - f0, r1 = v1 - f1;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(r1), "f"(r0));
+        w[1] = h;
     }
 }
 
-// One GEMM round, issued by one thread: D[half h] (TMEM columns h*K ..) = A[rows of half h] B.
-template <int PREC, int K>
-__device__ __forceinline__ void issue_round(unsigned char* A, size_t a_piece, unsigned char* Bm, size_t b_piece,
-                                            int halves, uint32_t tmem, uint64_t* bar)
+// Splits 8 values (times inv for the scaled variant) and stores their 16-byte line in every piece.
+template <int PREC, int A_PIECE>
+__device__ __forceinline__ void store_line(uint32_t a_smem, uint32_t off, const float* v, float inv)
 {
     using S = TcSplit<PREC>;
-    constexpr uint32_t idesc = umma_idesc(S::BF16, 128, K);
-    constexpr uint32_t sbo = (K / 8) * 128;
-    for (int h = 0; h < halves; ++h) {
+    constexpr int P = S::PIECES;
+    uint32_t w[P][4];
 #pragma unroll
-        for (int s = 0; s < K / 16; ++s) {
+    for (int j = 0; j < 4; ++j) {
+        uint32_t t[P];
+        if constexpr (S::SCALED) split_pair<PREC>(v[2 * j] * inv, v[2 * j + 1] * inv, t);
+        else split_pair<PREC>(v[2 * j], v[2 * j + 1], t);
+#pragma unroll
+        for (int p = 0; p < P; ++p) w[p][j] = t[p];
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_smem + p * A_PIECE + off), "r"(w[p][0]),
+                     "r"(w[p][1]), "r"(w[p][2]), "r"(w[p][3])
+                     : "memory");
+}
+
+// 16 consecutive TMEM columns of this thread's lane (warp-wide, 32x32b shape); not waited.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// One GEMM round, issued by one thread: D[half h] (TMEM columns h * tcol ..) = A[rows of half h] B
+// over the first `kuse` of the operand's KA columns, into `nout` output columns (B stored K-major,
+// KB columns per row). A_MN: A in MN-major core matrices.
+template <int PREC, bool A_MN, int KA, int KB>
+__device__ __forceinline__ void issue_round(uint32_t a_smem, uint32_t a_piece, uint32_t b_smem, uint32_t b_piece,
+                                            int halves, int kuse, int nout, uint32_t tmem, uint32_t tcol,
+                                            uint64_t* bar)
+{
+    using S = TcSplit<PREC>;
+    const uint32_t idesc = umma_idesc(S::BF16, 128, nout) | (A_MN ? (1u << 15) : 0u);
+    constexpr uint32_t sbo_a = (KA / 8) * 128, sbo_b = (KB / 8) * 128;
+    for (int h = 0; h < halves; ++h) {
+        for (int s = 0; s < kuse / 16; ++s) {
 #pragma unroll
             for (int i = 0; i < S::PRODUCTS; ++i) {
-                const uint64_t ad = umma_desc(A + S::pa(i) * a_piece + (size_t)h * 128 * K * 2 + s * 256, 128, sbo);
-                const uint64_t bd = umma_desc(Bm + S::pb(i) * b_piece + s * 256, 128, sbo);
-                umma_f16(tmem + (uint32_t)(h * K), ad, bd, idesc, (s > 0 || i > 0) ? 1u : 0u);
+                const uint64_t ad = umma_desc_u32(a_smem + S::pa(i) * a_piece + (uint32_t)h * 128 * KA * 2 + s * 256,
+                                                  128, sbo_a);
+                const uint64_t bd = umma_desc_u32(b_smem + S::pb(i) * b_piece + s * 256, 128, sbo_b);
+                umma_f16(tmem + (uint32_t)h * tcol, ad, bd, idesc, (s > 0 || i > 0) ? 1u : 0u);
             }
         }
     }
     umma_commit(bar);
 }
 
+// k1 of block blk of a job: its per-block band array, else band0 with the launch's inline changes
+__device__ __forceinline__ int tc_block_band(const OlsArgs& a, const OlsJob& job, int64_t blk)
+{
+    if (job.band) return job.band[blk];
+    int band = job.band0;
+    for (int i = 0; i < a.nchg; ++i)
+        if (a.chg_block[i] <= blk) band = a.chg_band[i];
+    return band;
+}
+
+// Resident CTAs per SM the N = 256 kernel is compiled for (its register budget); N = 512 is held
+// to three CTAs by shared memory.
+#ifndef VBW_TC_MIN_CTAS_256
+#define VBW_TC_MIN_CTAS_256 5
+#endif
+
 template <int N, int PREC, bool BATCH>
-__global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
+__global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3) ols_tc_kernel(const OlsArgs a)
 {
     using G = TcSmem<N, PREC>;
     using S = TcSplit<PREC>;
-    constexpr int R1 = G::R1, R2 = G::R2, K1 = 2 * R1, K2 = 2 * R2;
+    constexpr int R1 = G::R1, R2 = G::R2, K1 = 2 * R1, K2 = 2 * R2, GT = G::GT;
     constexpr int O = N / 4, M = N - O, D = O / 2;
     constexpr int H2 = kTcBlocks * R1 / kTcThreads;   // row halves of rounds 2-3 (1 or 2)
+    constexpr int L23 = R1 < 32 ? R1 : 32;            // lanes that hold one block in rounds 2-3
+    constexpr uint32_t AP = G::A_PIECE;
+    // kept outputs n = k1' + R2 k2' in [D, N - D): k2' in [D / R2, (N - D) / R2)
+    constexpr int KLO = D / R2, KHI = (N - D) / R2;
     static_assert(kTcBlocks * R2 == kTcThreads, "rounds 1 and 4 have one row per thread");
+    static_assert(D % R2 == 0, "the kept outputs are whole columns of round 4");
 
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* Abuf = sm + G::OFF_A;
-    unsigned char* B1 = sm + G::OFF_B1;
-    unsigned char* B2 = sm + G::OFF_B2;
-    float* Tb = reinterpret_cast<float*>(sm + G::OFF_T);
-    const float2* twA = reinterpret_cast<const float2*>(a.tc_tables + G::MAT_BYTES);   // [k1][n2]
-    const float2* twB = twA + N;                                                       // [k1'][k1]
+    const uint32_t sA = smem_u32(sm + G::OFF_A);
+    const uint32_t sB1 = smem_u32(sm + G::OFF_B1), sB2 = smem_u32(sm + G::OFF_B2), sB3 = smem_u32(sm + G::OFF_B3);
+    float* gtab = reinterpret_cast<float*>(sm + G::OFF_G);
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);
+    float* sc = reinterpret_cast<float*>(sm + G::OFF_SC);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + 8);
+    const float4* twA = reinterpret_cast<const float4*>(a.tc_tables + G::MAT_BYTES);   // [n2][k1], pairs
+    const float4* twB = twA + N / 2;                                                   // [k1][k1'], pairs
     const int tid = threadIdx.x, warp = tid >> 5;
 
     {
@@ -186,6 +283,7 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
         uint4* dst = reinterpret_cast<uint4*>(sm + G::OFF_B1);
         for (int i = tid; i < (int)(G::MAT_BYTES / 16); i += kTcThreads) dst[i] = src[i];
         for (int i = tid; i < a.LV; i += kTcThreads) Vs[i] = a.V[i];
+        for (int i = tid; i < kTcBlocks * GT; i += kTcThreads) gtab[i] = 0.f;
     }
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -203,17 +301,22 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
     const long long limit = a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles;
     uint32_t phase = 0;
     bool alive = true;
+    int gband = -1;   // band of this thread's gain-table slot (tid & 7) when it was last built
 
-    // MMA round: operands written -> issue -> bounded wait for the accumulator
-    auto round = [&](auto kc, unsigned char* Bm, size_t b_piece, int halves) -> bool {
-        constexpr int K = decltype(kc)::value;
+    // MMA round: operands written -> issue -> bounded wait for the accumulator. The barrier also
+    // returns the AND of every thread's `vote`.
+    auto round = [&](auto amn, auto ka, auto kb, uint32_t sB, uint32_t b_piece, int halves, int kuse,
+                     int nout, uint32_t tcol, int vote, int* vote_all) -> bool {
         fence_proxy_async_smem();
         tc_fence_before_sync();
-        __syncthreads();
+        const int all = __syncthreads_and(vote);
+        if (vote_all) *vote_all = all;
         if (tid == 0) {
             tc_fence_after_sync();
             // test hook (debug bit 0): no MMAs, so nothing arrives and the bounded wait runs out
-            if (!(a.debug & 1)) issue_round<PREC, K>(Abuf, G::A_PIECE, Bm, b_piece, halves, tmem, bar);
+            if (!(a.debug & 1))
+                issue_round<PREC, decltype(amn)::value, decltype(ka)::value, decltype(kb)::value>(
+                    sA, AP, sB, b_piece, halves, kuse, nout, tmem, tcol, bar);
         }
         bool ok = mbar_wait_bounded(bar, phase, limit);
         if (!__syncthreads_and(ok)) {
@@ -244,7 +347,6 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
         }
         const int64_t nsamp = job.nsamp;
         const int64_t nblocks = (nsamp + M - 1) / M;
-        float rs[H2];   // FP16 row scales of the current round's rows
 
         // ask L2 for the next tile's input span while this tile runs its four rounds
         if (tid == 0 && tile + 1 < te && (a.flags & kOlsNoBulk) == 0) {
@@ -268,164 +370,200 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
                 prefetch_l2_bulk(nj.in + e, (uint32_t)(cnt * sizeof(float2)));
         }
 
-        // ---- round 1 input: row tid = (b, n2), x_b(R2 n1 + n2), n1 < R1
+        // ---- gain table of block tid & 7 (rebuilt only when its band changes: eq. (FS_Hk_real) is
+        //      a re-indexing of V), and this block's vote for stopband pruning
+        int vote;
+        {
+            const int b = tid & 7;
+            const int64_t blk = blk0 + b;
+            const bool act = blk < nblocks;
+            const int band = act ? tc_block_band(a, job, blk) : gband;
+            if (act && band != gband) {
+                float* g = gtab + b * GT;
+                for (int kk = tid >> 3; kk <= N / 2; kk += kTcThreads / kTcBlocks)
+                    g[kk] = hr_gain(kk, band, a.LV, Vs) * (1.0f / N);
+                gband = band;
+            }
+            vote = !act || (band + a.LV - 1 <= N / 4 - 1);
+        }
+
+        // ---- round 1 input: row tid = (b, n2), x_b(R2 n1 + n2), n1 < R1 (K-major)
+        float s1 = 1.f;   // FP16: scale of this block's round-1 rows
         {
             const int b = tid / R2, n2 = tid % R2;
             const int64_t blk = blk0 + b;
             const int64_t s0 = blk * M - O;
             float v[K1];
-            float mx = 0.f;
+            const bool interior = blk < nblocks && s0 >= 0 && s0 + N <= nsamp;
+            if (__all_sync(0xffffffffu, interior)) {
+                const float2* sp = job.in + s0 + n2;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) {
-                const int64_t si = s0 + (int64_t)R2 * n1 + n2;
-                float2 x = make_float2(0.f, 0.f);
-                if (blk < nblocks) {
-                    if (si >= 0) {
-                        if (si < nsamp) x = ld_stream(job.in + si);
-                    } else if (job.tail_in) {
-                        x = job.tail_in[O + si];
-                    }
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const float2 x = ld_stream(sp + R2 * n1);
+                    v[n1] = x.x;
+                    v[R1 + n1] = x.y;
                 }
-                v[n1] = x.x;
-                v[R1 + n1] = x.y;
-                mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-            }
-            float inv = 1.f;
-            rs[0] = 1.f;
-            if constexpr (S::SCALED) row_scale(mx, rs[0], inv);
-            put_row<PREC, K1>(Abuf, G::A_PIECE, tid, v, inv);
-        }
-        if (!(alive = round(std::integral_constant<int, K1>{}, B1, G::B1_PIECE, 1))) break;
-
-        // ---- round 1 output: twiddle W_N^{n2 k1}, transpose to rows (b, k1)
-        {
-            const int b = tid / R2, n2 = tid % R2;
+            } else {
 #pragma unroll
-            for (int c = 0; c < K1; c += 32) {
-                float d[32];
-                tmem_ld32(lane_tmem + c, d);
-                // columns c..c+31 hold re (k1 < R1) then im; pair them after both halves are in
-                if constexpr (K1 == 32) {
-#pragma unroll
-                    for (int k1 = 0; k1 < R1; ++k1) {
-                        const float2 w = __ldg(twA + k1 * R2 + n2);
-                        const float re = d[k1] * rs[0], im = d[R1 + k1] * rs[0];
-                        float* row = Tb + (b * R1 + k1) * G::TROW1;
-                        row[n2] = re * w.x - im * w.y;
-                        row[R2 + n2] = re * w.y + im * w.x;
-                    }
-                } else {
-                    // K1 = 64: first ld holds re of k1 0..31, the second im of k1 0..31
-                    float* dst = Tb;
-#pragma unroll
-                    for (int k1 = 0; k1 < 32; ++k1) {
-                        // stash re in the transpose row, combine with im on the second pass
-                        float* row = dst + (b * R1 + k1) * G::TROW1;
-                        if (c == 0) {
-                            row[n2] = d[k1] * rs[0];
-                        } else {
-                            const float2 w = __ldg(twA + k1 * R2 + n2);
-                            const float re = row[n2], im = d[k1] * rs[0];
-                            row[n2] = re * w.x - im * w.y;
-                            row[R2 + n2] = re * w.y + im * w.x;
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const int64_t si = s0 + (int64_t)R2 * n1 + n2;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (blk < nblocks) {
+                        if (si >= 0) {
+                            if (si < nsamp) x = ld_stream(job.in + si);
+                        } else if (job.tail_in) {
+                            x = job.tail_in[O + si];
                         }
                     }
+                    v[n1] = x.x;
+                    v[R1 + n1] = x.y;
                 }
             }
-        }
-        tc_fence_before_sync();
-        __syncthreads();
-
-        // ---- round 2 input: rows (b, k1) from the transpose buffer
-#pragma unroll
-        for (int h = 0; h < H2; ++h) {
-            const int r = tid + h * kTcThreads;
-            const float* row = Tb + r * G::TROW1;
-            float v[K2];
-            float mx = 0.f;
-#pragma unroll
-            for (int i = 0; i < K2; ++i) {
-                v[i] = row[i];
-                mx = fmaxf(mx, fabsf(v[i]));
-            }
             float inv = 1.f;
-            rs[h] = 1.f;
-            if constexpr (S::SCALED) row_scale(mx, rs[h], inv);
-            if constexpr (G::ALIAS) __syncthreads();   // every transposed row read before overwriting
-            put_row<PREC, K2>(Abuf, G::A_PIECE, r, v, inv);
-        }
-        if (!(alive = round(std::integral_constant<int, K2>{}, B2, G::B2_PIECE, H2))) break;
-
-        // ---- round 2 output: X_b(k1 + R1 k2); gains H_R(k)/N; swap; round 3 input (same rows)
+            if constexpr (S::SCALED) {
+                float mx = 0.f;
 #pragma unroll
-        for (int h = 0; h < H2; ++h) {
-            const int r = tid + h * kTcThreads;
-            const int b = r / R1, k1 = r % R1;
-            const int64_t blk = blk0 + b;
-            int band = job.band0;
-            if (job.band) {
-                if (blk < nblocks) band = job.band[blk];
-            } else {
-                for (int i = 0; i < a.nchg; ++i)
-                    if (a.chg_block[i] <= blk) band = a.chg_band[i];
+                for (int i = 0; i < K1; ++i) mx = fmaxf(mx, fabsf(v[i]));
+                pow2_scale(lane_group_max<R2>(mx), s1, inv);
             }
-            float d[32];
-            tmem_ld32(lane_tmem + (uint32_t)(h * K2), d);
-            float v[K2];
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) {
-                const int k = k1 + R1 * k2;
-                const int kk = k <= N / 2 ? k : N - k;
-                const float g = hr_gain(kk, band, a.LV, Vs) * (1.0f / N) * rs[h];
-                v[k2] = g * d[R2 + k2];        // swap: new re = im
-                v[R2 + k2] = g * d[k2];        //       new im = re
-            }
-            float mx = 0.f;
-#pragma unroll
-            for (int i = 0; i < K2; ++i) mx = fmaxf(mx, fabsf(v[i]));
-            float inv = 1.f;
-            rs[h] = 1.f;
-            if constexpr (S::SCALED) row_scale(mx, rs[h], inv);
-            put_row<PREC, K2>(Abuf, G::A_PIECE, r, v, inv);
+            for (int c = 0; c < K1 / 8; ++c) store_line<PREC, AP>(sA, core_offset(tid, 8 * c, K1), v + 8 * c, inv);
         }
-        if (!(alive = round(std::integral_constant<int, K2>{}, B2, G::B2_PIECE, H2))) break;
+        int prune = 0;
+        if (!(alive = round(std::false_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, vote, &prune)))
+            break;
 
-        // ---- round 3 output: twiddle W_N^{k1 k1'}, transpose to rows (b, k1')
-#pragma unroll
-        for (int h = 0; h < H2; ++h) {
-            const int r = tid + h * kTcThreads;
-            const int b = r / R1, k1 = r % R1;
-            float d[32];
-            tmem_ld32(lane_tmem + (uint32_t)(h * K2), d);
-#pragma unroll
-            for (int kp = 0; kp < R2; ++kp) {
-                const float2 w = __ldg(twB + kp * R1 + k1);
-                const float re = d[kp] * rs[h], im = d[R2 + kp] * rs[h];
-                float* row = Tb + (b * R2 + kp) * G::TROW3;
-                row[k1] = re * w.x - im * w.y;
-                row[R1 + k1] = re * w.y + im * w.x;
-            }
-        }
-        tc_fence_before_sync();
-        __syncthreads();
-
-        // ---- round 4 input: rows (b, k1') = tid
+        // ---- round 1 output: twiddle W_N^{n2 k1}; rows (b, k1) of round 2 as MN-major lines
         {
-            const float* row = Tb + tid * G::TROW3;
-            float v[K1];
-            float mx = 0.f;
+            const int b = tid / R2, n2 = tid % R2;
+            float re[R1], im[R1];
 #pragma unroll
-            for (int i = 0; i < K1; ++i) {
-                v[i] = row[i];
-                mx = fmaxf(mx, fabsf(v[i]));
+            for (int c = 0; c < R1; c += 16) {
+                tmem_ld16(lane_tmem + c, re + c);
+                tmem_ld16(lane_tmem + R1 + c, im + c);
+            }
+            tmem_ld_wait();
+            const float4* tw = twA + n2 * (R1 / 2);
+#pragma unroll
+            for (int j = 0; j < R1 / 2; ++j) {
+                const float4 w = __ldg(tw + j);
+                float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
+                if constexpr (S::SCALED) {
+                    r0 *= s1; i0 *= s1; r1 *= s1; i1 *= s1;
+                }
+                re[2 * j] = r0 * w.x - i0 * w.y;
+                im[2 * j] = r0 * w.y + i0 * w.x;
+                re[2 * j + 1] = r1 * w.z - i1 * w.w;
+                im[2 * j + 1] = r1 * w.w + i1 * w.z;
             }
             float inv = 1.f;
-            rs[0] = 1.f;
-            if constexpr (S::SCALED) row_scale(mx, rs[0], inv);
-            if constexpr (G::ALIAS) __syncthreads();   // every transposed row read before overwriting
-            put_row<PREC, K1>(Abuf, G::A_PIECE, tid, v, inv);
+            if constexpr (S::SCALED) {
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < R1; ++i) mx = fmaxf(mx, fmaxf(fabsf(re[i]), fabsf(im[i])));
+                float s2;
+                pow2_scale(lane_group_max<R2>(mx), s2, inv);
+                if (n2 == 0) sc[b] = s2;
+            }
+#pragma unroll
+            for (int h = 0; h < R1 / 8; ++h) {
+                store_line<PREC, AP>(sA, mn_line_offset(b * R1 + 8 * h, n2, K2), re + 8 * h, inv);
+                store_line<PREC, AP>(sA, mn_line_offset(b * R1 + 8 * h, R2 + n2, K2), im + 8 * h, inv);
+            }
         }
-        if (!(alive = round(std::integral_constant<int, K1>{}, B1, G::B1_PIECE, 1))) break;
+        if (!(alive = round(std::true_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
+                            sB2, G::B2_PIECE, H2, K2, prune ? K2 / 2 : K2, K2, 1, nullptr)))
+            break;
+
+        // ---- round 2 output: X_b(k1 + R1 k2) in slot order; gains H_R(k)/N; swap; round-3 rows
+        float s3[H2];   // FP16: scale of this thread's round-3 rows
+#pragma unroll
+        for (int h = 0; h < H2; ++h) {
+            const int r = tid + h * kTcThreads;
+            const int b = r / R1, k1 = r % R1;
+            float d[K2];
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2), d);
+            if (!prune) tmem_ld16(lane_tmem + (uint32_t)(h * K2 + 16), d + 16);
+            tmem_ld_wait();
+            const uint32_t glo = smem_u32(gtab + b * GT + k1);
+            const uint32_t ghi = smem_u32(gtab + b * GT + N - k1);
+            float sc2 = 1.f;
+            if constexpr (S::SCALED) sc2 = sc[b];
+            float v[K2];
+            auto gain_swap = [&](auto sre) {
+                constexpr int s = decltype(sre)::value;
+                constexpr int k2 = tc_slot_bin(s);
+                float gk = k2 < R2 / 2 ? lds_f32(glo + 4 * R1 * k2) : lds_f32(ghi - 4 * R1 * k2);
+                if constexpr (S::SCALED) gk *= sc2;
+                v[s] = gk * d[s + 8];       // swap: new re = im
+                v[s + 8] = gk * d[s];       //       new im = re
+            };
+            static_for<0, 8>(gain_swap);
+            if (!prune) static_for<16, 24>(gain_swap);
+            float inv = 1.f;
+            s3[h] = 1.f;
+            if constexpr (S::SCALED) {
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(v[i]));
+                if (!prune) {
+#pragma unroll
+                    for (int i = 16; i < K2; ++i) mx = fmaxf(mx, fabsf(v[i]));
+                }
+                pow2_scale(lane_group_max<L23>(mx), s3[h], inv);
+            }
+            store_line<PREC, AP>(sA, core_offset(r, 0, K2), v, inv);
+            store_line<PREC, AP>(sA, core_offset(r, 8, K2), v + 8, inv);
+            if (!prune) {
+                store_line<PREC, AP>(sA, core_offset(r, 16, K2), v + 16, inv);
+                store_line<PREC, AP>(sA, core_offset(r, 24, K2), v + 24, inv);
+            }
+        }
+        if (!(alive = round(std::false_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
+                            sB3, G::B2_PIECE, H2, prune ? K2 / 2 : K2, K2, K2, 1, nullptr)))
+            break;
+
+        // ---- round 3 output: twiddle W_N^{k1 k1'}; rows (b, k1') of round 4 as MN-major lines
+#pragma unroll
+        for (int h = 0; h < H2; ++h) {
+            const int r = tid + h * kTcThreads;
+            const int b = r / R1, k1 = r % R1;
+            float re[R2], im[R2];
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2), re);
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2 + R2), im);
+            tmem_ld_wait();
+            const float4* tw = twB + k1 * (R2 / 2);
+#pragma unroll
+            for (int j = 0; j < R2 / 2; ++j) {
+                const float4 w = __ldg(tw + j);
+                float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
+                if constexpr (S::SCALED) {
+                    r0 *= s3[h]; i0 *= s3[h]; r1 *= s3[h]; i1 *= s3[h];
+                }
+                re[2 * j] = r0 * w.x - i0 * w.y;
+                im[2 * j] = r0 * w.y + i0 * w.x;
+                re[2 * j + 1] = r1 * w.z - i1 * w.w;
+                im[2 * j + 1] = r1 * w.w + i1 * w.z;
+            }
+            float inv = 1.f;
+            if constexpr (S::SCALED) {
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < R2; ++i) mx = fmaxf(mx, fmaxf(fabsf(re[i]), fabsf(im[i])));
+                float s4;
+                pow2_scale(lane_group_max<L23>(mx), s4, inv);
+                if (k1 == 0) sc[kTcBlocks + b] = s4;
+            }
+#pragma unroll
+            for (int hh = 0; hh < R2 / 8; ++hh) {
+                store_line<PREC, AP>(sA, mn_line_offset(b * R2 + 8 * hh, k1, K1), re + 8 * hh, inv);
+                store_line<PREC, AP>(sA, mn_line_offset(b * R2 + 8 * hh, R1 + k1, K1), im + 8 * hh, inv);
+            }
+        }
+        if (!(alive = round(std::true_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, 1, nullptr)))
+            break;
 
         // ---- round 4 output: z(n) = swap(Z(n)), n = k1' + R2 k2'; keep D <= n < D + M
         {
@@ -433,32 +571,24 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
             const int64_t blk = blk0 + b;
             float zr[R1], zi[R1];
 #pragma unroll
-            for (int c = 0; c < K1; c += 32) {
-                float d[32];
-                tmem_ld32(lane_tmem + c, d);
-                if constexpr (K1 == 32) {
-#pragma unroll
-                    for (int i = 0; i < R1; ++i) {
-                        zr[i] = d[R1 + i] * rs[0];   // swap
-                        zi[i] = d[i] * rs[0];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (c == 0) zi[i] = d[i] * rs[0];
-                        else zr[i] = d[i] * rs[0];
-                    }
-                }
+            for (int c = 0; c < R1; c += 16) {
+                tmem_ld16(lane_tmem + c, zr + c);
+                tmem_ld16(lane_tmem + R1 + c, zi + c);
             }
+            tmem_ld_wait();
+            float s4 = 1.f;
+            if constexpr (S::SCALED) s4 = sc[kTcBlocks + b];
             if (blk < nblocks) {
-                const int64_t obase = blk * M - D;
+                float2* dst = job.out + (blk * M - D) + kp;
+                if ((blk + 1) * M <= nsamp) {
 #pragma unroll
-                for (int k2 = 0; k2 < R1; ++k2) {
-                    const int n = kp + R2 * k2;
-                    if (n >= D && n < D + M) {
-                        const int64_t oi = obase + n;
-                        if (oi < nsamp) st_stream(job.out + oi, make_float2(zr[k2], zi[k2]));
-                    }
+                    for (int k2 = KLO; k2 < KHI; ++k2)
+                        st_stream(dst + R2 * k2, make_float2(zi[k2] * s4, zr[k2] * s4));
+                } else {
+                    const int64_t obase = blk * M - D + kp;
+#pragma unroll
+                    for (int k2 = KLO; k2 < KHI; ++k2)
+                        if (obase + R2 * k2 < nsamp) st_stream(dst + R2 * k2, make_float2(zi[k2] * s4, zr[k2] * s4));
                 }
                 // the rows of the job's last block hand the stream's last O input samples on
                 if ((blk + 1) * M >= nsamp && job.tail_out) {
@@ -472,8 +602,6 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
                 }
             }
         }
-        tc_fence_before_sync();
-        __syncthreads();
     }
 
     tc_fence_before_sync();
@@ -481,32 +609,51 @@ __global__ void __launch_bounds__(kTcThreads) ols_tc_kernel(const OlsArgs a)
     if (warp == 0) tmem_dealloc(tmem, kTcTmemCols);
 }
 
-// Per-plan table (device): the B pieces of the DFT-R1 and DFT-R2 matrices in the shared-memory
-// image, then the twiddles W_N^{ab} as [k1 < R1][n2 < R2] and [k1' < R2][k1 < R1]. Built in FP64.
+// Real-form DFT-R matrix entry for output (bin kq, part po) and input (bin nq, part pi):
+// [[Fr, -Fi], [Fi, Fr]] with F(k, n) = exp(-j 2 pi k n / R), from FP64 sincospi with the exponent
+// k n reduced exactly mod R.
+__device__ __forceinline__ double dft_real_entry(int R, int kq, int po, int nq, int pi)
+{
+    const long long e = ((long long)kq * nq) % R;
+    double sn, cs;
+    sincospi(-2.0 * (double)e / (double)R, &sn, &cs);
+    if (po == 0) return pi == 0 ? cs : -sn;   // yr = Fr xr - Fi xi
+    return pi == 0 ? sn : cs;                 // yi = Fi xr + Fr xi
+}
+
+// Per-plan table (device): the B pieces of the DFT-R1 matrix (rounds 1 and 4, natural order), the
+// DFT-R2 matrix of round 2 (natural inputs, slot-ordered outputs) and of round 3 (slot-ordered
+// inputs, natural outputs), all in the shared-memory image; then the twiddles W_N^{n2 k1} as
+// [n2 < R2][k1 < R1] and W_N^{k1 k1'} as [k1 < R1][k1' < R2]. Built in FP64.
 template <int N, int PREC>
 __global__ void tc_table_kernel(unsigned char* out)
 {
     using G = TcSmem<N, PREC>;
     using S = TcSplit<PREC>;
-    constexpr int R1 = G::R1, R2 = G::R2;
+    constexpr int R1 = G::R1, R2 = G::R2, K1 = 2 * R1, K2 = 2 * R2;
+    constexpr int n1 = K1 * K1, n2 = K2 * K2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr int n1 = (2 * R1) * (2 * R1), n2 = (2 * R2) * (2 * R2);
-    if (i < n1 + n2) {
-        const bool first = i < n1;
-        const int R = first ? R1 : R2;
-        const int j = first ? i : i - n1;
-        const int K = 2 * R;
-        const int row = j / K, col = j % K;   // out index, in index
-        // [[Fr, -Fi], [Fi, Fr]], F(k, n) = exp(-j 2 pi k n / R)
-        const int kq = row % R, nq = col % R;
-        const long long e = ((long long)kq * nq) % R;
-        double sn, cs;
-        sincospi(-2.0 * (double)e / (double)R, &sn, &cs);
+    if (i < n1 + 2 * n2) {
+        int K, row, col, which;
+        if (i < n1) {
+            which = 0; K = K1; row = i / K1; col = i % K1;
+        } else {
+            which = (i - n1) < n2 ? 1 : 2;
+            const int j = (i - n1) % n2;
+            K = K2; row = j / K2; col = j % K2;
+        }
         double w;
-        if (row < R) w = col < R ? cs : -sn;   // yr = Fr xr - Fi xi
-        else w = col < R ? sn : cs;            // yi = Fi xr + Fr xi
-        unsigned char* base = out + (first ? 0 : (size_t)S::PIECES * G::B1_PIECE);
-        const size_t piece = first ? G::B1_PIECE : G::B2_PIECE;
+        if (which == 0) {
+            w = dft_real_entry(R1, row % R1, row / R1, col % R1, col / R1);
+        } else if (which == 1) {
+            w = dft_real_entry(R2, tc_slot_bin(row), tc_slot_part(row), col % R2, col / R2);
+        } else {
+            w = dft_real_entry(R2, row % R2, row / R2, tc_slot_bin(col), tc_slot_part(col));
+        }
+        unsigned char* base = out + (which == 0 ? 0
+                                                : (size_t)S::PIECES * G::B1_PIECE +
+                                                      (size_t)(which - 1) * S::PIECES * G::B2_PIECE);
+        const size_t piece = which == 0 ? G::B1_PIECE : G::B2_PIECE;
         double rem = w;
         for (int p = 0; p < S::PIECES; ++p) {
             if constexpr (S::BF16) {
@@ -521,18 +668,17 @@ __global__ void tc_table_kernel(unsigned char* out)
         }
     }
     if (i < N) {
-        // twA[k1][n2] = W_N^{k1 n2}, twB[k1'][k1] = W_N^{k1' k1}
         float2* tw = reinterpret_cast<float2*>(out + G::MAT_BYTES);
         {
-            const int k1 = i / R2, q = i % R2;
-            const long long e = ((long long)k1 * q) % N;
+            const int q2 = i / R1, q1 = i % R1;   // [n2][k1]
+            const long long e = ((long long)q2 * q1) % N;
             double sn, cs;
             sincospi(-2.0 * (double)e / (double)N, &sn, &cs);
             tw[i] = make_float2((float)cs, (float)sn);
         }
         {
-            const int kp = i / R1, k1 = i % R1;
-            const long long e = ((long long)kp * k1) % N;
+            const int q1 = i / R2, q2 = i % R2;   // [k1][k1']
+            const long long e = ((long long)q1 * q2) % N;
             double sn, cs;
             sincospi(-2.0 * (double)e / (double)N, &sn, &cs);
             tw[N + i] = make_float2((float)cs, (float)sn);

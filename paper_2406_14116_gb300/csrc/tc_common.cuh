@@ -43,6 +43,17 @@ __device__ __forceinline__ uint64_t umma_desc(const void* base, uint32_t lbo, ui
     return d;
 }
 
+// The same descriptor from a 32-bit shared-memory address.
+__device__ __forceinline__ uint64_t umma_desc_u32(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B both BF16 (bf16 =
 // true) or both FP16, both K-major, shape M x N (M in {64, 128}, N a multiple of 8 up to 256).
 __host__ __device__ constexpr uint32_t umma_idesc(bool bf16, int M, int N)

@@ -23,13 +23,16 @@ def to_fp16(x):
     return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
 
 
+@pytest.mark.parametrize("a_mn", [False, True])
 @pytest.mark.parametrize("bf16", [True, False])
 @pytest.mark.parametrize("K,NN", [(32, 32), (64, 64), (32, 64), (64, 32)])
-def test_tcgen05_gemm_layout(cuda, bf16, K, NN):
-    g = np.random.default_rng(K * 100 + NN + bf16)
+def test_tcgen05_gemm_layout(cuda, bf16, K, NN, a_mn):
+    """One tcgen05 GEMM with A in K-major core matrices (rounds 1 and 3 of the OLS kernel) or in
+    MN-major core matrices (rounds 2 and 4) against a host GEMM with the same 16-bit rounding."""
+    g = np.random.default_rng(K * 100 + NN + bf16 + 7 * a_mn)
     A = g.uniform(-1, 1, (128, K)).astype(np.float32)
     B = g.uniform(-1, 1, (K, NN)).astype(np.float32)
-    D = vbw.vbw_debug_tc_gemm(A, B, bf16)
+    D = vbw.vbw_debug_tc_gemm(A, B, bf16, a_mn_major=a_mn)
     r = to_bf16 if bf16 else to_fp16
     ref = r(A).astype(np.float64) @ r(B).astype(np.float64)
     np.testing.assert_allclose(D, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
