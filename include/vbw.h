@@ -213,9 +213,8 @@ vbw_status vbw_debug_set(int flags);
 /* Test hook: D (128 x NN) = A (128 x K) B (K x NN) on the tensor cores through the operand
  * layouts, descriptors, TMEM accumulator and waits the tensor-core OLS kernel uses, with A and B
  * rounded once to 16 bits. flags: bit 0 set = bfloat16, clear = float16; bit 1 set = A stored in
- * MN-major core matrices (the layout of rounds 2 and 4), clear = K-major; bit 2 (with bit 1) =
- * the A descriptor's leading and stride byte offsets exchanged. K, NN in {32, 64}; host float
- * arrays, row-major. Synchronous; allocates. */
+ * MN-major core matrices (the layout of rounds 2 and 4), clear = K-major. K, NN in {32, 64}; host
+ * float arrays, row-major. Synchronous; allocates. */
 vbw_status vbw_debug_tc_gemm(int flags, int K, int NN, const float* A, const float* B, float* D);
 
 /* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
@@ -288,12 +287,16 @@ vbw_status vbw_ptvir_error(vbw_plan_t plan, const int* bands, int nbands, const 
  * library image. Every GPU that loads the library holds it until the
  * process exits.
  *
- * The first call on a device looks up that array's device address, with the device current. Make
- * that first call before any stream capture. Every call shares the array and rewrites its tables,
- * so calls that overlap on the GPU race: order them on one stream, or synchronize between them.
- * The call itself makes no cudaMalloc/cudaFree and calls no allocating library routine. Requests
- * beyond the array's capacity are rejected with VBW_ERR_INVALID_ARG; every geometry vbw_plan
- * accepts fits.
+ * The first call on a device looks up that array's device address, with the device current, and
+ * the library keeps that address for the life of the process: make the first call before any
+ * stream capture, and do not call this entry point on a device after a cudaDeviceReset of it.
+ * Every call shares the array: a call rewrites its tables unless they already hold the same
+ * geometry and transition table as the previous call on that device, so calls that overlap on the
+ * GPU race. Order them on one stream, or synchronize between them. The transition table reaches
+ * the GPU inside the launch parameters (no copy from host memory), so the call does not wait on
+ * the host for the stream. The call itself makes no cudaMalloc/cudaFree and calls no allocating
+ * library routine. Requests beyond the array's capacity are rejected with VBW_ERR_INVALID_ARG;
+ * every geometry vbw_plan accepts fits.
  *
  * Errors: VBW_ERR_INVALID_ARG, VBW_ERR_BAND_RANGE, VBW_ERR_CUDA. Device-side wait timeouts are not
  * reported by this call. */

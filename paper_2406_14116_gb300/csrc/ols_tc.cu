@@ -98,7 +98,8 @@ cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st)
 // ---- GEMM test: D (128 x NN) = A (128 x K) B (K x NN) with one rounding of A and B to 16 bits,
 // through the same descriptors, instruction descriptor, TMEM load and waits the OLS kernel uses.
 // flags: bit 0 BF16 (else FP16); bit 1 A in MN-major core matrices (as rounds 2 and 4 of the OLS
-// kernel take it), else K-major; bit 2 (with bit 1) the A descriptor's two byte offsets exchanged.
+// kernel take it), else K-major. Both layouts use 128 bytes between core matrices along K and
+// K/8 * 128 bytes between them along the rows (the descriptor's leading and stride offsets).
 template <bool BF16>
 __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const float* B, float* D, int K,
                                                              int NN, int flags, int* status)
@@ -135,10 +136,9 @@ __global__ void __launch_bounds__(128) tc_gemm_test_kernel(const float* A, const
     if (tid == 0) {
         const uint32_t idesc = umma_idesc(BF16, 128, NN) | (a_mn ? (1u << 15) : 0u);
         const uint32_t sbo = (uint32_t)(K / 8) * 128;
-        const bool swap = a_mn && (flags & 4);
         for (int s = 0; s < K / 16; ++s)
-            umma_f16(tmem, umma_desc(As + s * 256, swap ? sbo : 128, swap ? 128 : sbo),
-                     umma_desc(Bs + s * 256, 128, sbo), idesc, s > 0 ? 1u : 0u);
+            umma_f16(tmem, umma_desc(As + s * 256, 128, sbo), umma_desc(Bs + s * 256, 128, sbo), idesc,
+                     s > 0 ? 1u : 0u);
         umma_commit(bar);
     }
     bool ok = mbar_wait_bounded(bar, 0, kWaitLimitCycles);

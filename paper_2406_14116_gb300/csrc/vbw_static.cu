@@ -19,7 +19,6 @@
 
 // Plan-time table kernels of vbw_api.cu.
 __global__ void vbw_twiddle_kernel(float2* tw, int N, int T, int E);
-__global__ void vbw_round_table_kernel(const double* Vd, float* Vf, int LV);
 __global__ void vbw_halfphase_kernel(float2* ph, int N);
 
 namespace vbw {
@@ -37,16 +36,36 @@ constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 float2 =
 constexpr size_t kTwCap = 32768;
 constexpr size_t kVOff = kTwOff + kTwCap;    // transition table, float32: at most 4088 bytes
 constexpr size_t kVCap = 8192;
-constexpr size_t kVdOff = kVOff + kVCap;     // transition table as passed (double): <= 8176 bytes
-constexpr size_t kVdCap = 8192;
 constexpr size_t kScratchBytes = 64 * 1024;      // the whole array: 64 KiB per GPU
-static_assert(kVdOff + kVdCap <= kScratchBytes, "scratch layout exceeds the array");
+constexpr int kMaxLV = 1022;                     // N / 2 - 2 at N = 2048
+static_assert(kVOff + kVCap <= kScratchBytes, "scratch layout exceeds the array");
+static_assert(sizeof(float) * kMaxLV <= kVCap, "transition table exceeds its share");
 
 static __device__ __align__(256) unsigned char vbw_static_scratch[kScratchBytes];
+
+// The transition table travels to the GPU inside the launch parameters (8 KiB of the 32 KiB a
+// launch may carry): no copy from pageable host memory, so the call never waits on the host.
+struct StaticV {
+    double v[kMaxLV];
+};
+
+__global__ void static_round_v_kernel(const StaticV p, int LV, float* Vf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < LV) Vf[i] = (float)p.v[i];
+}
 
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch[kMaxDevices] = {};   // device address of the scratch, per device
+
+// What the scratch of each device holds (the last call's geometry and table), so that a call
+// with the same ones enqueues no table kernels.
+struct TableKey {
+    int N = 0, overlap = 0, LV = 0;
+    double V[kMaxLV];
+};
+TableKey g_key[kMaxDevices];
 
 vbw_status fail_static(vbw_status st, const char* msg) { return vbw::set_error(st, msg); }
 
@@ -85,7 +104,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     if (nsamples < 0) return fail_static(VBW_ERR_INVALID_ARG, "nsamples < 0");
     const int T = layout_T_of(N), E = N / T;
     const size_t tw_bytes = sizeof(float2) * ((size_t)T * (E + 2) + ((overlap & 1) ? half_phase_entries(N) : 0));
-    if (tw_bytes > kTwCap || sizeof(float) * (size_t)LV > kVCap || sizeof(double) * (size_t)LV > kVdCap)
+    if (tw_bytes > kTwCap || LV > kMaxLV)
         return fail_static(VBW_ERR_INVALID_ARG, "request exceeds the static scratch (64 KiB)");
     if (nsamples == 0) return vbw::set_error(VBW_OK, "");
     if (!in || !out) return fail_static(VBW_ERR_INVALID_ARG, "in/out is NULL");
@@ -105,18 +124,30 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     if (st != VBW_OK) return st;
     float2* tw = reinterpret_cast<float2*>(scratch + kTwOff);
     float* Vf = reinterpret_cast<float*>(scratch + kVOff);
-    double* Vd = reinterpret_cast<double*>(scratch + kVdOff);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // tables of this call (every call rewrites them)
-    if (cudaMemcpyAsync(Vd, V, sizeof(double) * LV, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return fail_static(VBW_ERR_CUDA, "table upload failed");
-    const int tw_entries = T * (E + 2);
-    vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
-    if (overlap & 1)
-        vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256, 0, s>>>(tw + tw_entries, N);
-    vbw_round_table_kernel<<<(LV + 255) / 256, 256, 0, s>>>(Vd, Vf, LV);
-    if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
+    // tables of this call, unless the scratch already holds them (same geometry and table)
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        TableKey& k = g_key[dev];
+        const bool same = k.N == N && k.overlap == overlap && k.LV == LV &&
+                          memcmp(k.V, V, sizeof(double) * (size_t)LV) == 0;
+        if (!same) {
+            k.N = 0;   // invalid until every table kernel is enqueued
+            StaticV pv;
+            memcpy(pv.v, V, sizeof(double) * (size_t)LV);
+            const int tw_entries = T * (E + 2);
+            vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
+            if (overlap & 1)
+                vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256, 0, s>>>(tw + tw_entries, N);
+            static_round_v_kernel<<<(LV + 255) / 256, 256, 0, s>>>(pv, LV, Vf);
+            if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
+            k.N = N;
+            k.overlap = overlap;
+            k.LV = LV;
+            memcpy(k.V, V, sizeof(double) * (size_t)LV);
+        }
+    }
 
     OlsArgs a;
     memset(&a, 0, sizeof(a));

@@ -323,14 +323,13 @@ def vbw_filter_static(N: int, overlap: int, transition_samples, band: int, inp, 
                                    _dev_ptr(out), nsamples, _stream_handle(cuda_stream)))
 
 
-def vbw_debug_tc_gemm(A: np.ndarray, B: np.ndarray, bf16: bool = True, a_mn_major: bool = False,
-                      swap_offsets: bool = False) -> np.ndarray:
+def vbw_debug_tc_gemm(A: np.ndarray, B: np.ndarray, bf16: bool = True, a_mn_major: bool = False) -> np.ndarray:
     """D = A B on the tensor cores (A 128 x K, B K x NN, float32 host arrays); A stored K-major or
     MN-major."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     D = np.empty((A.shape[0], B.shape[1]), dtype=np.float32)
-    flags = (1 if bf16 else 0) | (2 if a_mn_major else 0) | (4 if swap_offsets else 0)
+    flags = (1 if bf16 else 0) | (2 if a_mn_major else 0)
     _check(lib().vbw_debug_tc_gemm(flags, A.shape[1], B.shape[1], _host_ptr(A),
                                    _host_ptr(B), _host_ptr(D)))
     return D

@@ -53,3 +53,25 @@ def test_no_alloc_matches_existing_entry_point_on_two_calls(cuda):
         vbw.Batch([(plan, x, y_ref, band)]).run(stream)
         torch.cuda.synchronize()
         assert_parity(y_static.cpu().numpy(), y_ref.cpu().numpy(), what=f"N={N}")
+
+
+@pytest.mark.gpu
+def test_no_alloc_call_leaves_device_memory_unchanged(cuda):
+    """After a warm-up call, a call with another geometry (so its tables are rebuilt) and a call
+    that repeats it (tables reused) leave the device's free memory exactly where it was."""
+    torch = cuda
+    L = vbw.lib()
+    stream = torch.cuda.current_stream()
+    n = 200_000
+    x = torch.from_numpy(wl.complex_gaussian(43, 0, n)).cuda()
+    y = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    V1, V2 = wl.transition_table(44, 12), wl.transition_table(45, 10)
+    assert _call(L, 512, 128, V1, 50, x.data_ptr(), y.data_ptr(), n, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _call(L, 2048, 512, V2, 300, x.data_ptr(), y.data_ptr(), n, stream.cuda_stream) == 0
+    assert _call(L, 2048, 512, V2, 300, x.data_ptr(), y2.data_ptr(), n, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(y.view(torch.float32), y2.view(torch.float32))
