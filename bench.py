@@ -76,6 +76,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-mode", choices=["tuned", "per_plan", "mixed"], default="tuned",
+                    help="mixed-N batches: the autotuner's launch mode, or one forced")
     ap.add_argument("--no-configs", action="store_true",
                     help="channels workload: skip the record of the other four workloads")
     return ap.parse_args()
@@ -489,7 +491,11 @@ def native_run(args):
     side = torch.cuda.Stream()          # graphs cannot be captured on the default stream
     torch.cuda.set_stream(side)
     stream = side
-    if len(plans) > 1 and not args.no_tune:
+    forced = getattr(args, "batch_mode", "tuned")
+    if len(plans) > 1 and forced != "tuned":
+        batch.set_mode(vbw.VBW_BATCH_PER_PLAN if forced == "per_plan" else vbw.VBW_BATCH_MIXED)
+        cfg["batch_mode"] = {"mode": forced, "forced": True}
+    elif len(plans) > 1 and not args.no_tune:
         tm = tune.tune_mixed(torch, batch)
         names = {vbw.VBW_BATCH_PER_PLAN: "per_plan", vbw.VBW_BATCH_MIXED: "mixed"}
         cfg["batch_mode"] = {"mode": names.get(tm["mode"], tm["mode"]), "share": tm["share"],

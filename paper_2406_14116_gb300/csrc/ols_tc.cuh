@@ -110,7 +110,7 @@ struct TcSmem {
     static constexpr size_t OFF_BAR = OFF_SC + sizeof(float) * 2 * kTcBlocks;
     static constexpr size_t BYTES = OFF_BAR + 16;
     // per-plan device table: the B1, B2, B3 pieces (shared-memory image), then the FP32 twiddles
-    // W_N^{n2 k1} as [n2 < R2][k1 < R1] and W_N^{k1 k1'} as [k1 < R1][k1' < R2]
+    // W_N^{k1 n2} as [k1 < R1][n2 < R2] and W_N^{k1' k1} as [k1' < R2][k1 < R1]
     static constexpr size_t MAT_BYTES = (size_t)P * (B1_PIECE + 2 * B2_PIECE);
     static constexpr size_t TABLE_BYTES = MAT_BYTES + 2 * sizeof(float2) * N;
     static_assert(OFF_B1 % 128 == 0 && OFF_B2 % 128 == 0 && OFF_B3 % 128 == 0 && OFF_G % 16 == 0, "alignment");
@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
     float* sc = reinterpret_cast<float*>(sm + G::OFF_SC);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + 8);
-    const float4* twA = reinterpret_cast<const float4*>(a.tc_tables + G::MAT_BYTES);   // [n2][k1], pairs
-    const float4* twB = twA + N / 2;                                                   // [k1][k1'], pairs
+    // twiddles, read through L1 with the reading thread's index fastest (coalesced)
+    const float2* twA = reinterpret_cast<const float2*>(a.tc_tables + G::MAT_BYTES);   // [k1][n2]
+    const float2* twB = twA + N;                                                       // [k1'][k1]
     const int tid = threadIdx.x, warp = tid >> 5;
 
     {
@@ -444,10 +445,11 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
                 tmem_ld16(lane_tmem + R1 + c, im + c);
             }
             tmem_ld_wait();
-            const float4* tw = twA + n2 * (R1 / 2);
+            const float2* tw = twA + n2;
 #pragma unroll
             for (int j = 0; j < R1 / 2; ++j) {
-                const float4 w = __ldg(tw + j);
+                const float2 w0 = __ldg(tw + (2 * j) * R2), w1 = __ldg(tw + (2 * j + 1) * R2);
+                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
                 float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
                 if constexpr (S::SCALED) {
                     r0 *= s1; i0 *= s1; r1 *= s1; i1 *= s1;
@@ -533,10 +535,11 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
             tmem_ld16(lane_tmem + (uint32_t)(h * K2), re);
             tmem_ld16(lane_tmem + (uint32_t)(h * K2 + R2), im);
             tmem_ld_wait();
-            const float4* tw = twB + k1 * (R2 / 2);
+            const float2* tw = twB + k1;
 #pragma unroll
             for (int j = 0; j < R2 / 2; ++j) {
-                const float4 w = __ldg(tw + j);
+                const float2 w0 = __ldg(tw + (2 * j) * R1), w1 = __ldg(tw + (2 * j + 1) * R1);
+                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
                 float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
                 if constexpr (S::SCALED) {
                     r0 *= s3[h]; i0 *= s3[h]; r1 *= s3[h]; i1 *= s3[h];
@@ -623,8 +626,8 @@ __device__ __forceinline__ double dft_real_entry(int R, int kq, int po, int nq, 
 
 // Per-plan table (device): the B pieces of the DFT-R1 matrix (rounds 1 and 4, natural order), the
 // DFT-R2 matrix of round 2 (natural inputs, slot-ordered outputs) and of round 3 (slot-ordered
-// inputs, natural outputs), all in the shared-memory image; then the twiddles W_N^{n2 k1} as
-// [n2 < R2][k1 < R1] and W_N^{k1 k1'} as [k1 < R1][k1' < R2]. Built in FP64.
+// inputs, natural outputs), all in the shared-memory image; then the twiddles W_N^{k1 n2} as
+// [k1 < R1][n2 < R2] and W_N^{k1' k1} as [k1' < R2][k1 < R1]. Built in FP64.
 template <int N, int PREC>
 __global__ void tc_table_kernel(unsigned char* out)
 {
@@ -668,17 +671,18 @@ __global__ void tc_table_kernel(unsigned char* out)
         }
     }
     if (i < N) {
+        // twA[k1][n2] = W_N^{k1 n2}, twB[k1'][k1] = W_N^{k1' k1}
         float2* tw = reinterpret_cast<float2*>(out + G::MAT_BYTES);
         {
-            const int q2 = i / R1, q1 = i % R1;   // [n2][k1]
-            const long long e = ((long long)q2 * q1) % N;
+            const int k1 = i / R2, q = i % R2;
+            const long long e = ((long long)k1 * q) % N;
             double sn, cs;
             sincospi(-2.0 * (double)e / (double)N, &sn, &cs);
             tw[i] = make_float2((float)cs, (float)sn);
         }
         {
-            const int q1 = i / R2, q2 = i % R2;   // [k1][k1']
-            const long long e = ((long long)q1 * q2) % N;
+            const int kp = i / R1, k1 = i % R1;
+            const long long e = ((long long)kp * k1) % N;
             double sn, cs;
             sincospi(-2.0 * (double)e / (double)N, &sn, &cs);
             tw[N + i] = make_float2((float)cs, (float)sn);
