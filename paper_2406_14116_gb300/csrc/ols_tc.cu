@@ -20,7 +20,7 @@ static cudaError_t launch_tc_w(const OlsArgs& a, int sms, cudaStream_t st)
     // Resident CTAs per SM, from the SM's shared memory, registers and threads. (The occupancy
     // calculator reports one CTA per SM for this kernel, while four fit and run concurrently:
     // measured 43 -> 127 Gsamples/s for BF16 x3 at N = 256.) VBW_TC_CTAS (1..8) overrides it. At
-    // most the TMEM columns of one SM allow: every CTA holds kTcTmemCols per tile slot.
+    // most the TMEM columns of one SM allow: every CTA holds kTcTmemCols.
     int dev = 0, smem_sm = 0, smem_rsv = 0;
     cudaFuncAttributes fa;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -39,7 +39,7 @@ static cudaError_t launch_tc_w(const OlsArgs& a, int sms, cudaStream_t st)
         return (c >= 1 && c <= 8) ? c : 0;
     }();
     if (env_ctas) per_sm = env_ctas;
-    if (per_sm > 512 / (kTcTmemCols * G::SLOTS)) per_sm = 512 / (kTcTmemCols * G::SLOTS);
+    if (per_sm > 512 / kTcTmemCols) per_sm = 512 / kTcTmemCols;
     int64_t grid = (int64_t)per_sm * sms;
     if (grid > a.ntiles) grid = a.ntiles;
     if (grid <= 0) return cudaSuccess;

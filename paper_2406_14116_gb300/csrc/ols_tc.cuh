@@ -88,34 +88,27 @@ __host__ __device__ constexpr uint32_t mn_line_offset(int row0, int k, int K)
     return (uint32_t)(((row0 >> 3) * (K >> 3) + (k >> 3)) * 128 + (k & 7) * 16);
 }
 
-// Shared-memory plan of one CTA (bytes). A CTA keeps SLOTS tiles in flight (one per slot: its
-// own operand buffer, TMEM columns, mbarrier, gain tables and FP16 scales), so that one tile's
-// CUDA-core work runs while another tile's GEMMs execute.
+// Shared-memory plan of one CTA (bytes).
 template <int N, int PREC>
 struct TcSmem {
     static constexpr int R1 = TcGeom<N>::R1, R2 = TcGeom<N>::R2;
     static_assert(R2 == 16, "the slot order of rounds 2-3 assumes R2 = 16");
     static constexpr int P = TcSplit<PREC>::PIECES;
-    // two tiles in flight, except where the second operand buffer would cost a resident CTA
-    // (BF16 x6 at N = 512)
-    static constexpr int SLOTS = (N == 512 && PREC == kTcBf16x6) ? 1 : 2;
     static constexpr int A_PIECE = kTcBlocks * N * 2 * 2;          // rows x K = 16 N in every round
-    static constexpr int A_SLOT = P * A_PIECE;
     static constexpr int B1_PIECE = (2 * R1) * (2 * R1) * 2;       // DFT-R1 matrix, one piece
     static constexpr int B2_PIECE = (2 * R2) * (2 * R2) * 2;       // DFT-R2 matrices, one piece each
     // per-block gain table g(kk) = H_R / N, kk = 0..N/2; the stride is 16 banks mod 32 so that two
     // blocks read by one warp use disjoint banks
     static constexpr int GT = ((N / 2 + 1 + 31) / 32) * 32 + 16;
-    static constexpr int SC = 32;                                  // FP16 scales per slot
     static constexpr size_t OFF_A = 0;
-    static constexpr size_t OFF_B1 = OFF_A + (size_t)SLOTS * A_SLOT;
+    static constexpr size_t OFF_B1 = OFF_A + (size_t)P * A_PIECE;
     static constexpr size_t OFF_B2 = OFF_B1 + (size_t)P * B1_PIECE;    // round 2: slot-ordered outputs
     static constexpr size_t OFF_B3 = OFF_B2 + (size_t)P * B2_PIECE;    // round 3: slot-ordered inputs
     static constexpr size_t OFF_G = OFF_B3 + (size_t)P * B2_PIECE;
-    static constexpr size_t OFF_V = OFF_G + sizeof(float) * SLOTS * kTcBlocks * GT;
-    static constexpr size_t OFF_SC = OFF_V + sizeof(float) * (N / 2);
-    static constexpr size_t OFF_BAR = OFF_SC + sizeof(float) * SLOTS * SC;
-    static constexpr size_t BYTES = OFF_BAR + 8 * SLOTS + 8;
+    static constexpr size_t OFF_V = OFF_G + sizeof(float) * kTcBlocks * GT;
+    static constexpr size_t OFF_SC = OFF_V + sizeof(float) * (N / 2);  // FP16: block scales of A2, A4
+    static constexpr size_t OFF_BAR = OFF_SC + sizeof(float) * 2 * kTcBlocks;
+    static constexpr size_t BYTES = OFF_BAR + 16;
     // per-plan device table: the B1, B2, B3 pieces (shared-memory image), then the FP32 twiddles
     // W_N^{k1 n2} as [k1 < R1][n2 < R2] and W_N^{k1' k1} as [k1' < R2][k1 < R1]
     static constexpr size_t MAT_BYTES = (size_t)P * (B1_PIECE + 2 * B2_PIECE);
@@ -253,17 +246,17 @@ __device__ __forceinline__ int tc_block_band(const OlsArgs& a, const OlsJob& job
 }
 
 // Resident CTAs per SM the N = 256 kernel is compiled for (its register budget); N = 512 is held
-// by shared memory.
+// to three CTAs by shared memory.
 #ifndef VBW_TC_MIN_CTAS_256
-#define VBW_TC_MIN_CTAS_256 4
+#define VBW_TC_MIN_CTAS_256 5
 #endif
 
 template <int N, int PREC, bool BATCH>
-__global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2) ols_tc_kernel(const OlsArgs a)
+__global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3) ols_tc_kernel(const OlsArgs a)
 {
     using G = TcSmem<N, PREC>;
     using S = TcSplit<PREC>;
-    constexpr int R1 = G::R1, R2 = G::R2, K1 = 2 * R1, K2 = 2 * R2, GT = G::GT, SLOTS = G::SLOTS;
+    constexpr int R1 = G::R1, R2 = G::R2, K1 = 2 * R1, K2 = 2 * R2, GT = G::GT;
     constexpr int O = N / 4, M = N - O, D = O / 2;
     constexpr int H2 = kTcBlocks * R1 / kTcThreads;   // row halves of rounds 2-3 (1 or 2)
     constexpr int L23 = R1 < 32 ? R1 : 32;            // lanes that hold one block in rounds 2-3
@@ -274,13 +267,13 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2
     static_assert(D % R2 == 0, "the kept outputs are whole columns of round 4");
 
     extern __shared__ __align__(1024) unsigned char sm[];
-    const uint32_t sA0 = smem_u32(sm + G::OFF_A);
+    const uint32_t sA = smem_u32(sm + G::OFF_A);
     const uint32_t sB1 = smem_u32(sm + G::OFF_B1), sB2 = smem_u32(sm + G::OFF_B2), sB3 = smem_u32(sm + G::OFF_B3);
-    float* gtab0 = reinterpret_cast<float*>(sm + G::OFF_G);
+    float* gtab = reinterpret_cast<float*>(sm + G::OFF_G);
     float* Vs = reinterpret_cast<float*>(sm + G::OFF_V);
-    float* sc0 = reinterpret_cast<float*>(sm + G::OFF_SC);
-    uint64_t* bar0 = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + 8 * SLOTS);
+    float* sc = reinterpret_cast<float*>(sm + G::OFF_SC);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + G::OFF_BAR + 8);
     // twiddles, read through L1 with the reading thread's index fastest (coalesced)
     const float2* twA = reinterpret_cast<const float2*>(a.tc_tables + G::MAT_BYTES);   // [k1][n2]
     const float2* twB = twA + N;                                                       // [k1'][k1]
@@ -291,103 +284,83 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2
         uint4* dst = reinterpret_cast<uint4*>(sm + G::OFF_B1);
         for (int i = tid; i < (int)(G::MAT_BYTES / 16); i += kTcThreads) dst[i] = src[i];
         for (int i = tid; i < a.LV; i += kTcThreads) Vs[i] = a.V[i];
-        for (int i = tid; i < SLOTS * kTcBlocks * GT; i += kTcThreads) gtab0[i] = 0.f;
-        for (int i = tid; i < SLOTS * G::SC; i += kTcThreads) sc0[i] = 1.f;
+        for (int i = tid; i < kTcBlocks * GT; i += kTcThreads) gtab[i] = 0.f;
     }
     if (tid == 0) {
-        for (int s = 0; s < SLOTS; ++s) mbar_init(bar0 + s, 1);
+        mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        tmem_alloc(tslot, kTcTmemCols * SLOTS);
+        tmem_alloc(tslot, kTcTmemCols);
         tmem_relinquish();
     }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_tmem0 = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
     const long long limit = a.wait_limit > 0 ? a.wait_limit : kWaitLimitCycles;
-    uint32_t phases = 0;    // bit s: parity of slot s's next completion
-    uint32_t pending = 0;   // bit s: slot s has GEMMs issued and not yet waited for
-    uint32_t prunes = 0;    // bit s: slot s's tile prunes rounds 2-3
+    uint32_t phase = 0;
     bool alive = true;
-    int gband0 = -1, gband1 = -1;   // band of gain table (slot, tid & 7) when it was last built
+    int gband = -1;   // band of this thread's gain-table slot (tid & 7) when it was last built
 
-    // GEMM round r (0..3) of slot s: operands written -> barrier (returning the AND of `vote`)
-    // -> one thread issues into the slot's TMEM columns, completion on the slot's mbarrier.
-    auto issue = [&](int r, int s, int vote) -> int {
+    // MMA round: operands written -> issue -> bounded wait for the accumulator. The barrier also
+    // returns the AND of every thread's `vote`.
+    auto round = [&](auto amn, auto ka, auto kb, uint32_t sB, uint32_t b_piece, int halves, int kuse,
+                     int nout, uint32_t tcol, int vote, int* vote_all) -> bool {
         fence_proxy_async_smem();
         tc_fence_before_sync();
         const int all = __syncthreads_and(vote);
-        const bool pr = r == 0 ? all != 0 : ((prunes >> s) & 1u) != 0;
+        if (vote_all) *vote_all = all;
         if (tid == 0) {
             tc_fence_after_sync();
-            // test hook (debug bit 0): no GEMMs, so nothing arrives and the bounded wait runs out
-            if (!(a.debug & 1)) {
-                const uint32_t aS = sA0 + (uint32_t)s * G::A_SLOT;
-                const uint32_t tm = tmem + (uint32_t)s * kTcTmemCols;
-                uint64_t* b = bar0 + s;
-                if (r == 0)
-                    issue_round<PREC, false, K1, K1>(aS, AP, sB1, G::B1_PIECE, 1, K1, K1, tm, 0, b);
-                else if (r == 1)
-                    issue_round<PREC, true, K2, K2>(aS, AP, sB2, G::B2_PIECE, H2, K2, pr ? K2 / 2 : K2, tm, K2, b);
-                else if (r == 2)
-                    issue_round<PREC, false, K2, K2>(aS, AP, sB3, G::B2_PIECE, H2, pr ? K2 / 2 : K2, K2, tm, K2, b);
-                else
-                    issue_round<PREC, true, K1, K1>(aS, AP, sB1, G::B1_PIECE, 1, K1, K1, tm, 0, b);
-            }
+            // test hook (debug bit 0): no MMAs, so nothing arrives and the bounded wait runs out
+            if (!(a.debug & 1))
+                issue_round<PREC, decltype(amn)::value, decltype(ka)::value, decltype(kb)::value>(
+                    sA, AP, sB, b_piece, halves, kuse, nout, tmem, tcol, bar);
         }
-        pending |= 1u << s;
-        return all;
-    };
-    // bounded wait for slot s's GEMMs
-    auto wait = [&](int s) -> bool {
-        const uint32_t par = (phases >> s) & 1u;
-        const bool ok = mbar_wait_bounded(bar0 + s, par, limit);
+        bool ok = mbar_wait_bounded(bar, phase, limit);
         if (!__syncthreads_and(ok)) {
             if (tid == 0 && a.status) atomicOr(a.status, kStatusWaitTimeout);
+            mbar_wait_bounded(bar, phase, limit);   // the MMAs may still be running: wait once more
+            __syncthreads();
             return false;
         }
-        phases ^= 1u << s;
-        pending &= ~(1u << s);
+        phase ^= 1u;
         tc_fence_after_sync();
         return true;
-    };
-    // a tile's job and first block (loads through opaque pointers stay where they are written, so
-    // the descriptor is not held in registers across the GEMM rounds)
-    auto fetch = [&](int64_t t, OlsJob& j, int64_t& b0) {
-        if constexpr (BATCH) {
-            const int2 td = opaque(a.tiles)[t];
-            j = opaque(a.jobs)[td.x];
-            b0 = td.y;
-        } else {
-            j = a.job;
-            b0 = t * kTcBlocks;
-        }
     };
 
     const int64_t ntiles = a.ntiles;
     const int64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
     const int64_t tb = (int64_t)blockIdx.x * per + ((int64_t)blockIdx.x < extra ? blockIdx.x : extra);
     const int64_t te = tb + per + ((int64_t)blockIdx.x < extra ? 1 : 0);
-
-    // ---- stage 0 of tile t in slot s: gain tables (rebuilt only when a block's band changes:
-    //      eq. (FS_Hk_real) is a re-indexing of V) and the pruning vote; round-1 operand rows
-    //      (b, n2) = x_b(R2 n1 + n2), n1 < R1, K-major
-    auto stage_input = [&](int s, int64_t t) -> int {
+    for (int64_t tile = tb; tile < te && alive; ++tile) {
         OlsJob job;
         int64_t blk0;
-        fetch(t, job, blk0);
+        if constexpr (BATCH) {
+            const int2 td = a.tiles[tile];
+            job = a.jobs[td.x];
+            blk0 = td.y;
+        } else {
+            job = a.job;
+            blk0 = tile * kTcBlocks;
+        }
         const int64_t nsamp = job.nsamp;
         const int64_t nblocks = (nsamp + M - 1) / M;
-        float* sc = sc0 + s * G::SC;
 
-        // ask L2 for the input span of the tile this slot takes next
-        if (tid == 0 && t + SLOTS < te && (a.flags & kOlsNoBulk) == 0) {
+        // ask L2 for the next tile's input span while this tile runs its four rounds
+        if (tid == 0 && tile + 1 < te && (a.flags & kOlsNoBulk) == 0) {
             OlsJob nj;
             int64_t nb0;
-            fetch(t + SLOTS, nj, nb0);
+            if constexpr (BATCH) {
+                const int2 nd = a.tiles[tile + 1];
+                nj = a.jobs[nd.x];
+                nb0 = nd.y;
+            } else {
+                nj = a.job;
+                nb0 = (tile + 1) * kTcBlocks;
+            }
             int64_t e = nb0 * M - O;
             int64_t e2 = (nb0 + kTcBlocks) * M;
             if (e < 0) e = 0;
@@ -398,144 +371,140 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2
                 prefetch_l2_bulk(nj.in + e, (uint32_t)(cnt * sizeof(float2)));
         }
 
+        // ---- gain table of block tid & 7 (rebuilt only when its band changes: eq. (FS_Hk_real) is
+        //      a re-indexing of V), and this block's vote for stopband pruning
         int vote;
         {
             const int b = tid & 7;
             const int64_t blk = blk0 + b;
             const bool act = blk < nblocks;
-            int gb = s ? gband1 : gband0;
-            const int band = act ? tc_block_band(a, job, blk) : gb;
-            if (act && band != gb) {
-                float* g = gtab0 + (s * kTcBlocks + b) * GT;
+            const int band = act ? tc_block_band(a, job, blk) : gband;
+            if (act && band != gband) {
+                float* g = gtab + b * GT;
                 for (int kk = tid >> 3; kk <= N / 2; kk += kTcThreads / kTcBlocks)
                     g[kk] = hr_gain(kk, band, a.LV, Vs) * (1.0f / N);
-                gb = band;
+                gband = band;
             }
-            if (s) gband1 = gb;
-            else gband0 = gb;
             vote = !act || (band + a.LV - 1 <= N / 4 - 1);
         }
 
-        const int b = tid / R2, n2 = tid % R2;
-        const int64_t blk = blk0 + b;
-        const int64_t s0 = blk * M - O;
-        float v[K1];
-        const bool interior = blk < nblocks && s0 >= 0 && s0 + N <= nsamp;
-        if (__all_sync(0xffffffffu, interior)) {
-            const float2* sp = job.in + s0 + n2;
+        // ---- round 1 input: row tid = (b, n2), x_b(R2 n1 + n2), n1 < R1 (K-major)
+        float s1 = 1.f;   // FP16: scale of this block's round-1 rows
+        {
+            const int b = tid / R2, n2 = tid % R2;
+            const int64_t blk = blk0 + b;
+            const int64_t s0 = blk * M - O;
+            float v[K1];
+            const bool interior = blk < nblocks && s0 >= 0 && s0 + N <= nsamp;
+            if (__all_sync(0xffffffffu, interior)) {
+                const float2* sp = job.in + s0 + n2;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) {
-                const float2 x = ld_stream(sp + R2 * n1);
-                v[n1] = x.x;
-                v[R1 + n1] = x.y;
-            }
-        } else {
-#pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) {
-                const int64_t si = s0 + (int64_t)R2 * n1 + n2;
-                float2 x = make_float2(0.f, 0.f);
-                if (blk < nblocks) {
-                    if (si >= 0) {
-                        if (si < nsamp) x = ld_stream(job.in + si);
-                    } else if (job.tail_in) {
-                        x = job.tail_in[O + si];
-                    }
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const float2 x = ld_stream(sp + R2 * n1);
+                    v[n1] = x.x;
+                    v[R1 + n1] = x.y;
                 }
-                v[n1] = x.x;
-                v[R1 + n1] = x.y;
+            } else {
+#pragma unroll
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const int64_t si = s0 + (int64_t)R2 * n1 + n2;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (blk < nblocks) {
+                        if (si >= 0) {
+                            if (si < nsamp) x = ld_stream(job.in + si);
+                        } else if (job.tail_in) {
+                            x = job.tail_in[O + si];
+                        }
+                    }
+                    v[n1] = x.x;
+                    v[R1 + n1] = x.y;
+                }
             }
-        }
-        float inv = 1.f;
-        if constexpr (S::SCALED) {
-            float mx = 0.f;
-#pragma unroll
-            for (int i = 0; i < K1; ++i) mx = fmaxf(mx, fabsf(v[i]));
-            float s1;
-            pow2_scale(lane_group_max<R2>(mx), s1, inv);
-            if (n2 == 0) sc[16 + b] = s1;
-        }
-        const uint32_t aS = sA0 + (uint32_t)s * G::A_SLOT;
-#pragma unroll
-        for (int c = 0; c < K1 / 8; ++c) store_line<PREC, AP>(aS, core_offset(tid, 8 * c, K1), v + 8 * c, inv);
-        return vote;
-    };
-
-    // ---- round 1 output of slot s: twiddle W_N^{n2 k1}; rows (b, k1) of round 2 as MN-major lines
-    auto stage_epi1 = [&](int s) {
-        float* sc = sc0 + s * G::SC;
-        const uint32_t aS = sA0 + (uint32_t)s * G::A_SLOT;
-        const uint32_t lt = lane_tmem0 + (uint32_t)s * kTcTmemCols;
-        const int b = tid / R2, n2 = tid % R2;
-        float re[R1], im[R1];
-#pragma unroll
-        for (int c = 0; c < R1; c += 16) {
-            tmem_ld16(lt + c, re + c);
-            tmem_ld16(lt + R1 + c, im + c);
-        }
-        tmem_ld_wait();
-        float s1 = 1.f;
-        if constexpr (S::SCALED) s1 = sc[16 + b];
-        const float2* tw = twA + n2;
-#pragma unroll
-        for (int j = 0; j < R1 / 2; ++j) {
-            const float2 w0 = __ldg(tw + (2 * j) * R2), w1 = __ldg(tw + (2 * j + 1) * R2);
-            float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
+            float inv = 1.f;
             if constexpr (S::SCALED) {
-                r0 *= s1; i0 *= s1; r1 *= s1; i1 *= s1;
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < K1; ++i) mx = fmaxf(mx, fabsf(v[i]));
+                pow2_scale(lane_group_max<R2>(mx), s1, inv);
             }
-            re[2 * j] = r0 * w0.x - i0 * w0.y;
-            im[2 * j] = r0 * w0.y + i0 * w0.x;
-            re[2 * j + 1] = r1 * w1.x - i1 * w1.y;
-            im[2 * j + 1] = r1 * w1.y + i1 * w1.x;
-        }
-        float inv = 1.f;
-        if constexpr (S::SCALED) {
-            float mx = 0.f;
 #pragma unroll
-            for (int i = 0; i < R1; ++i) mx = fmaxf(mx, fmaxf(fabsf(re[i]), fabsf(im[i])));
-            float s2;
-            pow2_scale(lane_group_max<R2>(mx), s2, inv);
-            if (n2 == 0) sc[b] = s2;
+            for (int c = 0; c < K1 / 8; ++c) store_line<PREC, AP>(sA, core_offset(tid, 8 * c, K1), v + 8 * c, inv);
         }
-#pragma unroll
-        for (int h = 0; h < R1 / 8; ++h) {
-            store_line<PREC, AP>(aS, mn_line_offset(b * R1 + 8 * h, n2, K2), re + 8 * h, inv);
-            store_line<PREC, AP>(aS, mn_line_offset(b * R1 + 8 * h, R2 + n2, K2), im + 8 * h, inv);
-        }
-    };
+        int prune = 0;
+        if (!(alive = round(std::false_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, vote, &prune)))
+            break;
 
-    // ---- round 2 output of slot s: X_b(k1 + R1 k2) in slot order; gains H_R(k)/N; swap;
-    //      round-3 rows, K-major
-    auto stage_epi2 = [&](int s) {
-        float* sc = sc0 + s * G::SC;
-        const uint32_t aS = sA0 + (uint32_t)s * G::A_SLOT;
-        const uint32_t lt = lane_tmem0 + (uint32_t)s * kTcTmemCols;
-        const bool prune = ((prunes >> s) & 1u) != 0;
+        // ---- round 1 output: twiddle W_N^{n2 k1}; rows (b, k1) of round 2 as MN-major lines
+        {
+            const int b = tid / R2, n2 = tid % R2;
+            float re[R1], im[R1];
+#pragma unroll
+            for (int c = 0; c < R1; c += 16) {
+                tmem_ld16(lane_tmem + c, re + c);
+                tmem_ld16(lane_tmem + R1 + c, im + c);
+            }
+            tmem_ld_wait();
+            const float2* tw = twA + n2;
+#pragma unroll
+            for (int j = 0; j < R1 / 2; ++j) {
+                const float2 w0 = __ldg(tw + (2 * j) * R2), w1 = __ldg(tw + (2 * j + 1) * R2);
+                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
+                float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
+                if constexpr (S::SCALED) {
+                    r0 *= s1; i0 *= s1; r1 *= s1; i1 *= s1;
+                }
+                re[2 * j] = r0 * w.x - i0 * w.y;
+                im[2 * j] = r0 * w.y + i0 * w.x;
+                re[2 * j + 1] = r1 * w.z - i1 * w.w;
+                im[2 * j + 1] = r1 * w.w + i1 * w.z;
+            }
+            float inv = 1.f;
+            if constexpr (S::SCALED) {
+                float mx = 0.f;
+#pragma unroll
+                for (int i = 0; i < R1; ++i) mx = fmaxf(mx, fmaxf(fabsf(re[i]), fabsf(im[i])));
+                float s2;
+                pow2_scale(lane_group_max<R2>(mx), s2, inv);
+                if (n2 == 0) sc[b] = s2;
+            }
+#pragma unroll
+            for (int h = 0; h < R1 / 8; ++h) {
+                store_line<PREC, AP>(sA, mn_line_offset(b * R1 + 8 * h, n2, K2), re + 8 * h, inv);
+                store_line<PREC, AP>(sA, mn_line_offset(b * R1 + 8 * h, R2 + n2, K2), im + 8 * h, inv);
+            }
+        }
+        if (!(alive = round(std::true_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
+                            sB2, G::B2_PIECE, H2, K2, prune ? K2 / 2 : K2, K2, 1, nullptr)))
+            break;
+
+        // ---- round 2 output: X_b(k1 + R1 k2) in slot order; gains H_R(k)/N; swap; round-3 rows
+        float s3[H2];   // FP16: scale of this thread's round-3 rows
 #pragma unroll
         for (int h = 0; h < H2; ++h) {
             const int r = tid + h * kTcThreads;
             const int b = r / R1, k1 = r % R1;
             float d[K2];
-            tmem_ld16(lt + (uint32_t)(h * K2), d);
-            if (!prune) tmem_ld16(lt + (uint32_t)(h * K2 + 16), d + 16);
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2), d);
+            if (!prune) tmem_ld16(lane_tmem + (uint32_t)(h * K2 + 16), d + 16);
             tmem_ld_wait();
-            const float* g = gtab0 + (s * kTcBlocks + b) * GT;
-            const uint32_t glo = smem_u32(g + k1);
-            const uint32_t ghi = smem_u32(g + N - k1);
+            const uint32_t glo = smem_u32(gtab + b * GT + k1);
+            const uint32_t ghi = smem_u32(gtab + b * GT + N - k1);
             float sc2 = 1.f;
             if constexpr (S::SCALED) sc2 = sc[b];
             float v[K2];
             auto gain_swap = [&](auto sre) {
-                constexpr int sl = decltype(sre)::value;
-                constexpr int k2 = tc_slot_bin(sl);
+                constexpr int s = decltype(sre)::value;
+                constexpr int k2 = tc_slot_bin(s);
                 float gk = k2 < R2 / 2 ? lds_f32(glo + 4 * R1 * k2) : lds_f32(ghi - 4 * R1 * k2);
                 if constexpr (S::SCALED) gk *= sc2;
-                v[sl] = gk * d[sl + 8];       // swap: new re = im
-                v[sl + 8] = gk * d[sl];       //       new im = re
+                v[s] = gk * d[s + 8];       // swap: new re = im
+                v[s + 8] = gk * d[s];       //       new im = re
             };
             static_for<0, 8>(gain_swap);
             if (!prune) static_for<16, 24>(gain_swap);
             float inv = 1.f;
+            s3[h] = 1.f;
             if constexpr (S::SCALED) {
                 float mx = 0.f;
 #pragma unroll
@@ -544,46 +513,41 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2
 #pragma unroll
                     for (int i = 16; i < K2; ++i) mx = fmaxf(mx, fabsf(v[i]));
                 }
-                float s3;
-                pow2_scale(lane_group_max<L23>(mx), s3, inv);
-                if (k1 == 0) sc[24 + b] = s3;
+                pow2_scale(lane_group_max<L23>(mx), s3[h], inv);
             }
-            store_line<PREC, AP>(aS, core_offset(r, 0, K2), v, inv);
-            store_line<PREC, AP>(aS, core_offset(r, 8, K2), v + 8, inv);
+            store_line<PREC, AP>(sA, core_offset(r, 0, K2), v, inv);
+            store_line<PREC, AP>(sA, core_offset(r, 8, K2), v + 8, inv);
             if (!prune) {
-                store_line<PREC, AP>(aS, core_offset(r, 16, K2), v + 16, inv);
-                store_line<PREC, AP>(aS, core_offset(r, 24, K2), v + 24, inv);
+                store_line<PREC, AP>(sA, core_offset(r, 16, K2), v + 16, inv);
+                store_line<PREC, AP>(sA, core_offset(r, 24, K2), v + 24, inv);
             }
         }
-    };
+        if (!(alive = round(std::false_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
+                            sB3, G::B2_PIECE, H2, prune ? K2 / 2 : K2, K2, K2, 1, nullptr)))
+            break;
 
-    // ---- round 3 output of slot s: twiddle W_N^{k1 k1'}; rows (b, k1') of round 4 as MN-major lines
-    auto stage_epi3 = [&](int s) {
-        float* sc = sc0 + s * G::SC;
-        const uint32_t aS = sA0 + (uint32_t)s * G::A_SLOT;
-        const uint32_t lt = lane_tmem0 + (uint32_t)s * kTcTmemCols;
+        // ---- round 3 output: twiddle W_N^{k1 k1'}; rows (b, k1') of round 4 as MN-major lines
 #pragma unroll
         for (int h = 0; h < H2; ++h) {
             const int r = tid + h * kTcThreads;
             const int b = r / R1, k1 = r % R1;
             float re[R2], im[R2];
-            tmem_ld16(lt + (uint32_t)(h * K2), re);
-            tmem_ld16(lt + (uint32_t)(h * K2 + R2), im);
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2), re);
+            tmem_ld16(lane_tmem + (uint32_t)(h * K2 + R2), im);
             tmem_ld_wait();
-            float s3 = 1.f;
-            if constexpr (S::SCALED) s3 = sc[24 + b];
             const float2* tw = twB + k1;
 #pragma unroll
             for (int j = 0; j < R2 / 2; ++j) {
                 const float2 w0 = __ldg(tw + (2 * j) * R1), w1 = __ldg(tw + (2 * j + 1) * R1);
+                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
                 float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
                 if constexpr (S::SCALED) {
-                    r0 *= s3; i0 *= s3; r1 *= s3; i1 *= s3;
+                    r0 *= s3[h]; i0 *= s3[h]; r1 *= s3[h]; i1 *= s3[h];
                 }
-                re[2 * j] = r0 * w0.x - i0 * w0.y;
-                im[2 * j] = r0 * w0.y + i0 * w0.x;
-                re[2 * j + 1] = r1 * w1.x - i1 * w1.y;
-                im[2 * j + 1] = r1 * w1.y + i1 * w1.x;
+                re[2 * j] = r0 * w.x - i0 * w.y;
+                im[2 * j] = r0 * w.y + i0 * w.x;
+                re[2 * j + 1] = r1 * w.z - i1 * w.w;
+                im[2 * j + 1] = r1 * w.w + i1 * w.z;
             }
             float inv = 1.f;
             if constexpr (S::SCALED) {
@@ -596,91 +560,56 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 2
             }
 #pragma unroll
             for (int hh = 0; hh < R2 / 8; ++hh) {
-                store_line<PREC, AP>(aS, mn_line_offset(b * R2 + 8 * hh, k1, K1), re + 8 * hh, inv);
-                store_line<PREC, AP>(aS, mn_line_offset(b * R2 + 8 * hh, R1 + k1, K1), im + 8 * hh, inv);
+                store_line<PREC, AP>(sA, mn_line_offset(b * R2 + 8 * hh, k1, K1), re + 8 * hh, inv);
+                store_line<PREC, AP>(sA, mn_line_offset(b * R2 + 8 * hh, R1 + k1, K1), im + 8 * hh, inv);
             }
         }
-    };
+        if (!(alive = round(std::true_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, 1, nullptr)))
+            break;
 
-    // ---- round 4 output of tile t in slot s: z(n) = swap(Z(n)), n = k1' + R2 k2'; keep
-    //      D <= n < D + M; the accumulator is read in chunks of 16 columns k2'
-    auto stage_out = [&](int s, int64_t t) {
-        OlsJob job;
-        int64_t blk0;
-        fetch(t, job, blk0);
-        const int64_t nsamp = job.nsamp;
-        const int64_t nblocks = (nsamp + M - 1) / M;
-        const float* sc = sc0 + s * G::SC;
-        const uint32_t lt = lane_tmem0 + (uint32_t)s * kTcTmemCols;
-        const int b = tid / R2, kp = tid % R2;
-        const int64_t blk = blk0 + b;
-        float s4 = 1.f;
-        if constexpr (S::SCALED) s4 = sc[kTcBlocks + b];
-        const bool act = blk < nblocks;
-        const bool full = (blk + 1) * M <= nsamp;
-        float2* dst = job.out + (blk * M - D) + kp;
-        const int64_t obase = blk * M - D + kp;
+        // ---- round 4 output: z(n) = swap(Z(n)), n = k1' + R2 k2'; keep D <= n < D + M
+        {
+            const int b = tid / R2, kp = tid % R2;
+            const int64_t blk = blk0 + b;
+            float zr[R1], zi[R1];
 #pragma unroll
-        for (int c = 0; c < R1; c += 16) {
-            float zr[16], zi[16];
-            tmem_ld16(lt + c, zr);
-            tmem_ld16(lt + R1 + c, zi);
+            for (int c = 0; c < R1; c += 16) {
+                tmem_ld16(lane_tmem + c, zr + c);
+                tmem_ld16(lane_tmem + R1 + c, zi + c);
+            }
             tmem_ld_wait();
-            if (act) {
+            float s4 = 1.f;
+            if constexpr (S::SCALED) s4 = sc[kTcBlocks + b];
+            if (blk < nblocks) {
+                float2* dst = job.out + (blk * M - D) + kp;
+                if ((blk + 1) * M <= nsamp) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int k2 = c + i;
-                    if (k2 < KLO || k2 >= KHI) continue;
-                    if (full || obase + R2 * k2 < nsamp)
-                        st_stream(dst + R2 * k2, make_float2(zi[i] * s4, zr[i] * s4));
+                    for (int k2 = KLO; k2 < KHI; ++k2)
+                        st_stream(dst + R2 * k2, make_float2(zi[k2] * s4, zr[k2] * s4));
+                } else {
+                    const int64_t obase = blk * M - D + kp;
+#pragma unroll
+                    for (int k2 = KLO; k2 < KHI; ++k2)
+                        if (obase + R2 * k2 < nsamp) st_stream(dst + R2 * k2, make_float2(zi[k2] * s4, zr[k2] * s4));
+                }
+                // the rows of the job's last block hand the stream's last O input samples on
+                if ((blk + 1) * M >= nsamp && job.tail_out) {
+                    for (int i = kp; i < O; i += R2) {
+                        const int64_t si = nsamp - O + i;
+                        float2 x = make_float2(0.f, 0.f);
+                        if (si >= 0) x = job.in[si];
+                        else if (job.tail_in) x = job.tail_in[O + si];
+                        job.tail_out[i] = x;
+                    }
                 }
             }
         }
-        // the rows of the job's last block hand the stream's last O input samples on
-        if (act && (blk + 1) * M >= nsamp && job.tail_out) {
-            for (int i = kp; i < O; i += R2) {
-                const int64_t si = nsamp - O + i;
-                float2 x = make_float2(0.f, 0.f);
-                if (si >= 0) x = job.in[si];
-                else if (job.tail_in) x = job.tail_in[O + si];
-                job.tail_out[i] = x;
-            }
-        }
-    };
-
-    // Tiles in groups of SLOTS, one per slot; every stage of one slot runs while the other slot's
-    // GEMMs execute.
-    for (int64_t t0 = tb; t0 < te && alive; t0 += SLOTS) {
-        const int ns = (int)((te - t0) < SLOTS ? (te - t0) : SLOTS);
-#pragma unroll 1
-        for (int s = 0; s < ns; ++s) {
-            const int vote = stage_input(s, t0 + s);
-            const int all = issue(0, s, vote);
-            prunes = (prunes & ~(1u << s)) | ((all ? 1u : 0u) << s);
-        }
-#pragma unroll 1
-        for (int r = 1; r <= 4 && alive; ++r) {
-#pragma unroll 1
-            for (int s = 0; s < ns; ++s) {
-                if (!(alive = wait(s))) break;
-                if (r == 1) stage_epi1(s);
-                else if (r == 2) stage_epi2(s);
-                else if (r == 3) stage_epi3(s);
-                else stage_out(s, t0 + s);
-                if (r < 4) issue(r, s, 1);
-            }
-        }
-    }
-    if (!alive) {
-        // a wait ran out: give the GEMMs still in flight one more bounded wait before the TMEM
-        // columns are freed
-        for (int s = 0; s < SLOTS; ++s)
-            if ((pending >> s) & 1u) mbar_wait_bounded(bar0 + s, (phases >> s) & 1u, limit);
     }
 
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTcTmemCols * SLOTS);
+    if (warp == 0) tmem_dealloc(tmem, kTcTmemCols);
 }
 
 // Real-form DFT-R matrix entry for output (bin kq, part po) and input (bin nq, part pi):
