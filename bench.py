@@ -84,6 +84,7 @@ def parse_args():
 
 
 KERNEL_SOURCES = ("ols_fp32.cuh", "fft_reg.cuh", "vbw_common.cuh")   # the fused FP32 kernel
+TC_SOURCES = ("ols_tc.cuh", "tc_common.cuh") + KERNEL_SOURCES             # the tensor-core kernel
 OLA_SOURCES = KERNEL_SOURCES + ("vbw_ola.cu",)                        # the overlap-add kernel
 
 
@@ -120,14 +121,14 @@ def source_hash(files=None) -> str:
     return h.hexdigest()[:12]
 
 
-def profile_traffic(kernel_tag: str, files=None):
+def profile_traffic(kernel_tag: str, files=None, key: str = "dram_bytes_per_full_launch"):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on this source."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_h = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    m_t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    m_t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     if not m_h or not m_t or m_h.group(1) != source_hash(files):
         return None
     return float(m_t.group(1))
@@ -567,6 +568,9 @@ def native_run(args):
     achieved = BYTES_PER_SAMPLE * total / (step_ms / 1e3) / 1e9
     tag = {"channels": "ols_fp32_n1024_channels"}.get(args.workload, f"ols_fp32_{args.workload}")
     traffic = profile_traffic(tag)
+    if args.workload == "precision" and args.prec == "bf16" and not args.channels and not args.samples:
+        traffic = profile_traffic("ols_tc_n256-512_bf16_precision", TC_SOURCES,
+                                  key=f"dram_bytes_per_full_launch_n{args.N}")
 
     e2e = None
     if not args.no_e2e:
@@ -967,15 +971,22 @@ def config_records(args):
         _INPUT_CACHE.clear()
         torch.cuda.empty_cache()
 
-        # serving: 2000 streams, Poisson arrivals at 50k chunks/s for a few seconds, then saturation
-        a = sub(workload="serving", duration=5.0)
-        line = serving_run(a)
+        # serving: 2000 streams, Poisson arrivals at 50k chunks/s for a few seconds, then saturation;
+        # in a process of its own, so that the other workloads' host threads and memory do not
+        # stall its arrival loop
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serving", "--duration", "5",
+               "--rate", str(args.rate), "--pool-mb", str(args.pool_mb), "--slots", str(args.slots)]
+        proc = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+        lines = [x for x in proc.stdout.splitlines() if x.startswith("{")]
+        if proc.returncode != 0 or not lines:
+            raise RuntimeError(f"serving run failed (rc {proc.returncode}): {proc.stderr[-300:]}")
+        line = json.loads(lines[-1])
         out["serving"] = {
             "workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
             "latency_ms": line["latency_ms"], "offered_gsamples_s": line["offered_gsamples_s"],
             "saturation_gsamples_s": line["saturation_gsamples_s"], "chunks": line["steps"],
             "batches": line["batches"], "gpu_launches": line["gpu_launches"],
-            "clocks": line["clocks"],
+            "clocks": line["clocks"], "process": "separate (python bench.py --workload serving)",
             "parity": "tests/test_serving_gpu.py (per-stream oracle parity, alone vs mixed bit-equal)",
         }
     except Exception as e:   # the headline stands; the record says what failed
