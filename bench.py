@@ -326,17 +326,17 @@ def oracle_blocks(oracle, V, s, x, b0, nb):
 
 def pick_runs(streams, g, run_len, count):
     """(stream index, first block) of runs of consecutive blocks: the first stream's start, the
-    last stream's ragged end, then seeded positions."""
+    last stream's ragged end, then seeded positions. A workload with fewer than count x run_len
+    blocks is covered whole, by non-overlapping runs."""
+    nbs = [(s.nsamples + s.N - s.overlap - 1) // (s.N - s.overlap) for s in streams]
+    if sum(nbs) <= count * run_len:
+        return [(i, b0) for i, nb in enumerate(nbs) for b0 in range(0, nb, run_len)]
     runs = [(0, 0)]
     last = len(streams) - 1
-    M = streams[last].N - streams[last].overlap
-    nbl = (streams[last].nsamples + M - 1) // M
-    runs.append((last, max(0, nbl - run_len)))
+    runs.append((last, max(0, nbs[last] - run_len)))
     while len(runs) < count:
         i = int(g.integers(0, len(streams)))
-        M = streams[i].N - streams[i].overlap
-        nbi = (streams[i].nsamples + M - 1) // M
-        runs.append((i, int(g.integers(0, max(1, nbi - run_len)))))
+        runs.append((i, int(g.integers(0, max(1, nbs[i] - run_len)))))
     return runs
 
 
