@@ -12,8 +12,6 @@
 //   any other w = c + j s           "tangent" form w v = c ((v.x - t v.y) + j (v.y + t v.x)) with
 //                                   t = s/c (or the cotangent form when |s| > |c|, so |t| <= 1):
 //                                   2 FFMA for the rotation + 4 FFMA for u +- c(.)  = 6
-// fft_reg_gain<R, INV>(a, g) is fft_reg on the input g(n) a(n) (real gains), with the gains
-// folded into the first stage: g_lo a_lo +- g_hi a_hi = 2 FMUL + 4 FFMA per pair.
 #pragma once
 
 #include "vbw_common.cuh"
@@ -132,26 +130,6 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[R])
         dit_stages<R, 1, INV>(b);
         static_for<0, R>([&](auto i) { a[i] = b[i]; });
     }
-}
-
-// fft_reg of (g(n) a(n)): the first DIT stage pairs natural indices (i, i + R/2), which sit at
-// bit-reversed positions (2m, 2m + 1); the gains enter there as FMUL/FFMA factors.
-template <int R, bool INV>
-__device__ __forceinline__ void fft_reg_gain(float2 (&a)[R], const float (&g)[R])
-{
-    static_assert(R >= 2 && (R & (R - 1)) == 0, "radix-2 codelet needs a power of two >= 2");
-    float2 b[R];
-    static_for<0, R / 2>([&](auto m) {
-        constexpr int lo = 2 * decltype(m)::value, hi = lo + 1;
-        constexpr int nlo = bit_reverse<R>(lo), nhi = bit_reverse<R>(hi);
-        const float2 x = a[nlo], y = a[nhi];
-        const float gl = g[nlo], gh = g[nhi];
-        const float px = gl * x.x, py = gl * x.y;
-        b[lo] = make_float2(fmaf(gh, y.x, px), fmaf(gh, y.y, py));
-        b[hi] = make_float2(fmaf(-gh, y.x, px), fmaf(-gh, y.y, py));
-    });
-    if constexpr (R > 2) dit_stages<R, 2, INV>(b);
-    static_for<0, R>([&](auto i) { a[i] = b[i]; });
 }
 
 }  // namespace vbw
