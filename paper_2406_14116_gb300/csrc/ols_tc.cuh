@@ -245,10 +245,11 @@ __device__ __forceinline__ int tc_block_band(const OlsArgs& a, const OlsJob& job
     return band;
 }
 
-// Resident CTAs per SM the N = 256 kernel is compiled for (its register budget); N = 512 is held
-// to three CTAs by shared memory.
+// Resident CTAs per SM the N = 256 kernel is compiled for (its register budget: 4 CTAs leave 128
+// registers, enough for the tables each epilogue loads while the GEMMs run); N = 512 is held to
+// three CTAs by shared memory.
 #ifndef VBW_TC_MIN_CTAS_256
-#define VBW_TC_MIN_CTAS_256 5
+#define VBW_TC_MIN_CTAS_256 4
 #endif
 
 template <int N, int PREC, bool BATCH>
@@ -304,10 +305,11 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
     bool alive = true;
     int gband = -1;   // band of this thread's gain-table slot (tid & 7) when it was last built
 
-    // MMA round: operands written -> issue -> bounded wait for the accumulator. The barrier also
-    // returns the AND of every thread's `vote`.
+    // MMA round: operands written -> issue -> `pre` (loads the next epilogue's tables while the
+    // GEMMs run) -> bounded wait for the accumulator. The barrier also returns the AND of every
+    // thread's `vote`.
     auto round = [&](auto amn, auto ka, auto kb, uint32_t sB, uint32_t b_piece, int halves, int kuse,
-                     int nout, uint32_t tcol, int vote, int* vote_all) -> bool {
+                     int nout, uint32_t tcol, int vote, int* vote_all, auto&& pre) -> bool {
         fence_proxy_async_smem();
         tc_fence_before_sync();
         const int all = __syncthreads_and(vote);
@@ -319,6 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
                 issue_round<PREC, decltype(amn)::value, decltype(ka)::value, decltype(kb)::value>(
                     sA, AP, sB, b_piece, halves, kuse, nout, tmem, tcol, bar);
         }
+        pre();
         bool ok = mbar_wait_bounded(bar, phase, limit);
         if (!__syncthreads_and(ok)) {
             if (tid == 0 && a.status) atomicOr(a.status, kStatusWaitTimeout);
@@ -431,8 +434,13 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
             for (int c = 0; c < K1 / 8; ++c) store_line<PREC, AP>(sA, core_offset(tid, 8 * c, K1), v + 8 * c, inv);
         }
         int prune = 0;
+        float2 tw1[R1];   // W_N^{n2 k1}, k1 < R1, for this thread's round-1 row
         if (!(alive = round(std::false_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
-                            sB1, G::B1_PIECE, 1, K1, K1, 0, vote, &prune)))
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, vote, &prune, [&] {
+                                const float2* tw = twA + tid % R2;
+#pragma unroll
+                                for (int k = 0; k < R1; ++k) tw1[k] = __ldg(tw + k * R2);
+                            })))
             break;
 
         // ---- round 1 output: twiddle W_N^{n2 k1}; rows (b, k1) of round 2 as MN-major lines
@@ -445,11 +453,9 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
                 tmem_ld16(lane_tmem + R1 + c, im + c);
             }
             tmem_ld_wait();
-            const float2* tw = twA + n2;
 #pragma unroll
             for (int j = 0; j < R1 / 2; ++j) {
-                const float2 w0 = __ldg(tw + (2 * j) * R2), w1 = __ldg(tw + (2 * j + 1) * R2);
-                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
+                const float4 w = make_float4(tw1[2 * j].x, tw1[2 * j].y, tw1[2 * j + 1].x, tw1[2 * j + 1].y);
                 float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
                 if constexpr (S::SCALED) {
                     r0 *= s1; i0 *= s1; r1 *= s1; i1 *= s1;
@@ -474,8 +480,26 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
                 store_line<PREC, AP>(sA, mn_line_offset(b * R1 + 8 * h, R2 + n2, K2), im + 8 * h, inv);
             }
         }
+        // gains of this thread's round-2 rows: gp[h][i] for slot i (outer bins) and slot i + 8
+        // (inner bins, i >= 8), read from the block's table while the GEMMs run
+        float gp[H2][16];
         if (!(alive = round(std::true_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
-                            sB2, G::B2_PIECE, H2, K2, prune ? K2 / 2 : K2, K2, 1, nullptr)))
+                            sB2, G::B2_PIECE, H2, K2, prune ? K2 / 2 : K2, K2, 1, nullptr, [&] {
+#pragma unroll
+                                for (int h = 0; h < H2; ++h) {
+                                    const int r = tid + h * kTcThreads;
+                                    const int b = r / R1, k1 = r % R1;
+                                    const uint32_t glo = smem_u32(gtab + b * GT + k1);
+                                    const uint32_t ghi = smem_u32(gtab + b * GT + N - k1);
+                                    auto load = [&](auto ii) {
+                                        constexpr int i = decltype(ii)::value;
+                                        constexpr int k2 = tc_slot_bin(i < 8 ? i : i + 8);
+                                        gp[h][i] = k2 < R2 / 2 ? lds_f32(glo + 4 * R1 * k2) : lds_f32(ghi - 4 * R1 * k2);
+                                    };
+                                    static_for<0, 8>(load);
+                                    if (!prune) static_for<8, 16>(load);
+                                }
+                            })))
             break;
 
         // ---- round 2 output: X_b(k1 + R1 k2) in slot order; gains H_R(k)/N; swap; round-3 rows
@@ -483,20 +507,17 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
 #pragma unroll
         for (int h = 0; h < H2; ++h) {
             const int r = tid + h * kTcThreads;
-            const int b = r / R1, k1 = r % R1;
+            const int b = r / R1;
             float d[K2];
             tmem_ld16(lane_tmem + (uint32_t)(h * K2), d);
             if (!prune) tmem_ld16(lane_tmem + (uint32_t)(h * K2 + 16), d + 16);
             tmem_ld_wait();
-            const uint32_t glo = smem_u32(gtab + b * GT + k1);
-            const uint32_t ghi = smem_u32(gtab + b * GT + N - k1);
             float sc2 = 1.f;
             if constexpr (S::SCALED) sc2 = sc[b];
             float v[K2];
             auto gain_swap = [&](auto sre) {
                 constexpr int s = decltype(sre)::value;
-                constexpr int k2 = tc_slot_bin(s);
-                float gk = k2 < R2 / 2 ? lds_f32(glo + 4 * R1 * k2) : lds_f32(ghi - 4 * R1 * k2);
+                float gk = gp[h][s < 8 ? s : s - 8];
                 if constexpr (S::SCALED) gk *= sc2;
                 v[s] = gk * d[s + 8];       // swap: new re = im
                 v[s + 8] = gk * d[s];       //       new im = re
@@ -522,8 +543,16 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
                 store_line<PREC, AP>(sA, core_offset(r, 24, K2), v + 24, inv);
             }
         }
+        float2 tw3[H2][R2];   // W_N^{k1 k1'}, k1' < R2, for this thread's round-3 rows
         if (!(alive = round(std::false_type{}, std::integral_constant<int, K2>{}, std::integral_constant<int, K2>{},
-                            sB3, G::B2_PIECE, H2, prune ? K2 / 2 : K2, K2, K2, 1, nullptr)))
+                            sB3, G::B2_PIECE, H2, prune ? K2 / 2 : K2, K2, K2, 1, nullptr, [&] {
+#pragma unroll
+                                for (int h = 0; h < H2; ++h) {
+                                    const float2* tw = twB + (tid + h * kTcThreads) % R1;
+#pragma unroll
+                                    for (int k = 0; k < R2; ++k) tw3[h][k] = __ldg(tw + k * R1);
+                                }
+                            })))
             break;
 
         // ---- round 3 output: twiddle W_N^{k1 k1'}; rows (b, k1') of round 4 as MN-major lines
@@ -535,11 +564,9 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
             tmem_ld16(lane_tmem + (uint32_t)(h * K2), re);
             tmem_ld16(lane_tmem + (uint32_t)(h * K2 + R2), im);
             tmem_ld_wait();
-            const float2* tw = twB + k1;
 #pragma unroll
             for (int j = 0; j < R2 / 2; ++j) {
-                const float2 w0 = __ldg(tw + (2 * j) * R1), w1 = __ldg(tw + (2 * j + 1) * R1);
-                const float4 w = make_float4(w0.x, w0.y, w1.x, w1.y);
+                const float4 w = make_float4(tw3[h][2 * j].x, tw3[h][2 * j].y, tw3[h][2 * j + 1].x, tw3[h][2 * j + 1].y);
                 float r0 = re[2 * j], i0 = im[2 * j], r1 = re[2 * j + 1], i1 = im[2 * j + 1];
                 if constexpr (S::SCALED) {
                     r0 *= s3[h]; i0 *= s3[h]; r1 *= s3[h]; i1 *= s3[h];
@@ -565,7 +592,7 @@ __global__ void __launch_bounds__(kTcThreads, N == 256 ? VBW_TC_MIN_CTAS_256 : 3
             }
         }
         if (!(alive = round(std::true_type{}, std::integral_constant<int, K1>{}, std::integral_constant<int, K1>{},
-                            sB1, G::B1_PIECE, 1, K1, K1, 0, 1, nullptr)))
+                            sB1, G::B1_PIECE, 1, K1, K1, 0, 1, nullptr, [] {})))
             break;
 
         // ---- round 4 output: z(n) = swap(Z(n)), n = k1' + R2 k2'; keep D <= n < D + M
