@@ -1,7 +1,8 @@
 // Blackwell 5th-generation tensor-core helpers (tcgen05, inline PTX) for the DFT-as-GEMM variant.
 //
 // One thread issues tcgen05.mma with both operands in shared memory (UMMA matrix descriptors,
-// no swizzle, K-major), the FP32 accumulator lives in tensor memory (TMEM), completion is
+// no swizzle; B K-major, A K-major or MN-major), the FP32 accumulator lives in tensor memory
+// (TMEM), completion is
 // signalled on an mbarrier through tcgen05.commit, and the four warps of a warpgroup read the
 // accumulator rows back with tcgen05.ld (warp w owns TMEM lanes 32w .. 32w+31).
 //
@@ -56,6 +57,7 @@ __device__ __forceinline__ uint64_t umma_desc_u32(uint32_t saddr, uint32_t lbo, 
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B both BF16 (bf16 =
 // true) or both FP16, both K-major, shape M x N (M in {64, 128}, N a multiple of 8 up to 256).
+// Bit 15 set makes A MN-major (the caller ORs it in).
 __host__ __device__ constexpr uint32_t umma_idesc(bool bf16, int M, int N)
 {
     return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
@@ -122,9 +124,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// ---- 16-bit operand pieces
-// BF16: v ~ hi + lo (+ lo2 for three pieces), each piece the bf16 rounding of what is left.
-// FP16: the same on v scaled into [-1, 1] by a power of two chosen per row.
+// ---- 16-bit rounding of single values (the GEMM test hook; the OLS kernel splits pairs of
+// values into pieces with packed conversions, ols_tc.cuh)
 template <bool BF16>
 struct Half16;
 template <>
