@@ -313,6 +313,17 @@ struct WarpState {
     bool ntd_ok;
 };
 
+// CARRY (signals in host memory, read over the host link): the last O input samples of a block
+// are the first O of the next, and the same thread holds them (rows 3E/4..E-1 become rows
+// 0..E/4-1 when the overlap is N/4 and one block fills a warp-tile). They are kept in registers,
+// so consecutive blocks of a warp read each input sample from the link once instead of 4/3 times.
+template <int NC>
+struct CarryState {
+    float2 v[NC > 0 ? NC : 1];   // this thread's rows of the last O samples of the previous block
+    const float2* in;            // the signal they belong to; nullptr = none
+    int64_t blk;                 // the block that starts with them
+};
+
 // Per-launch switches of a warp-tile.
 struct TileCtl {
     bool bulk;            // bulk L2 prefetch allowed (signals in device memory)
@@ -325,14 +336,16 @@ struct TileCtl {
 // first block's output and the imaginary part the second's. blk counts pairs, and the band is
 // one per pair.
 // One warp-tile: 32/T blocks of plan `plan`, transform size N.
-template <int N, bool QOVL, class Src, bool REAL = false>
+template <int N, bool QOVL, class Src, bool REAL = false, bool CARRY = false>
 __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_next, int plan,
                                          const float2* tw_plan, const float* V, int LV, int O_rt,
                                          unsigned char* wbase, int lane, WarpState& ws,
-                                         const TileCtl& ctl)
+                                         const TileCtl& ctl,
+                                         CarryState<CARRY ? OlsGeom<N>::E / 4 : 0>* cs = nullptr)
 {
     using G = OlsGeom<N>;
     constexpr int E = G::E, T = G::T, B = G::B;
+    static_assert(!CARRY || (QOVL && !REAL && B == 1), "the carry needs overlap N/4 and one block per warp-tile");
     const int bsub = lane / T, t = lane % T;
     float2* buf = reinterpret_cast<float2*>(wbase + G::BUF_OFF) + bsub * G::BLK;
     float* gtab = reinterpret_cast<float*>(wbase + G::GAIN_OFF) + bsub * G::GT;
@@ -404,7 +417,17 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
             }
         } else if (__all_sync(0xffffffffu, interior)) {
             const float2* sp = job.in + s0 + t;
-            static_for<0, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
+            if constexpr (CARRY) {
+                // the block's first O samples are the previous block's last O (same warp, same rows)
+                if (cs->in == job.in && cs->blk == blk) {
+                    static_for<0, E / 4>([&](auto n1) { x[n1] = cs->v[n1]; });
+                    static_for<E / 4, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
+                } else {
+                    static_for<0, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
+                }
+            } else {
+                static_for<0, E>([&](auto n1) { x[n1] = ld_stream(sp + decltype(n1)::value * T); });
+            }
         } else {
             static_for<0, E>([&](auto n1) {
                 const int64_t si = s0 + decltype(n1)::value * T + t;
@@ -418,6 +441,13 @@ __device__ __forceinline__ void ols_tile(const Src& src, int64_t tile, bool has_
                 }
                 x[n1] = v;
             });
+        }
+
+        if constexpr (CARRY) {
+            // samples M .. N-1 of this span (rows 3E/4 .. E-1) open the next block's span
+            static_for<0, E / 4>([&](auto i) { cs->v[i] = x[3 * E / 4 + decltype(i)::value]; });
+            cs->in = active ? job.in : nullptr;
+            cs->blk = blk + 1;
         }
 
         // ---- ask L2 for the samples the warp's next tile adds (the rest is this span). The bulk
@@ -588,7 +618,7 @@ __device__ __forceinline__ void warp_range(int64_t ntiles, int64_t nwarps, int64
 // Each warp takes one contiguous range of tiles, so consecutive blocks of a stream stay in one
 // warp: the overlap samples are L2 hits and the gain table survives until the band changes.
 // QOVL: the overlap is N/4 (D = N/8, M = 3N/4) as a compile-time constant; otherwise a.overlap.
-template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false, bool CARRY = false>
 __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
 {
     using G = OlsGeom<N>;
@@ -605,22 +635,25 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
 
     WarpState ws{-1, make_int2(0, 0), false};
     const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
+    CarryState<CARRY ? G::E / 4 : 0> cs;
+    cs.in = nullptr;
+    cs.blk = -1;
     int64_t tb, te;
     warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
         if constexpr (BATCH)
-            ols_tile<N, QOVL, JobListSource, REAL>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0,
-                                                   tw_s, a.V, a.LV, a.overlap, wbase, lane, ws, ctl);
+            ols_tile<N, QOVL, JobListSource, REAL, CARRY>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0,
+                                                          tw_s, a.V, a.LV, a.overlap, wbase, lane, ws, ctl, &cs);
         else
             ols_tile<N, QOVL>(SingleJobSource{a}, tile, tile + 1 < te, 0, tw_s, a.V, a.LV, a.overlap,
                               wbase, lane, ws, ctl);
     }
 }
 
-template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false, bool CARRY = false>
 __global__ void VBW_OLS_BOUNDS(WARPS) ols_fp32_kernel(const OlsArgs a)
 {
-    ols_fp32_body<N, WARPS, QOVL, BATCH, REAL>(a);
+    ols_fp32_body<N, WARPS, QOVL, BATCH, REAL, CARRY>(a);
 }
 
 // N = 2048: registers capped so that three 4-warp CTAs (12 warps) are resident per SM
@@ -716,7 +749,7 @@ cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles,
     return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(warps * 32), args, smem, st);
 }
 
-template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false>
+template <int N, int WARPS, bool QOVL, bool BATCH, bool REAL = false, bool CARRY = false>
 cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStream_t st, int* grid_out)
 {
     const size_t smem = ols_smem_bytes<N>(WARPS) +
@@ -725,8 +758,8 @@ cudaError_t launch_ols_fp32_w(const OlsArgs& a, int sms, int max_ctas, cudaStrea
         return launch_persistent(ols_fp32_kernel_2048<WARPS, QOVL, BATCH, REAL>, WARPS, smem, a.ntiles, sms,
                                  max_ctas, st, grid_out, &a);
     else
-        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH, REAL>, WARPS, smem, a.ntiles, sms,
-                                 max_ctas, st, grid_out, &a);
+        return launch_persistent(ols_fp32_kernel<N, WARPS, QOVL, BATCH, REAL, CARRY>, WARPS, smem, a.ntiles,
+                                 sms, max_ctas, st, grid_out, &a);
 }
 
 template <int N>
@@ -746,6 +779,17 @@ cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, 
     if (!q) {   // any other even overlap: runtime geometry, 4 warps per CTA
         return b ? launch_ols_fp32_w<N, 4, false, true>(a, sms, max_ctas, st, grid_out)
                  : launch_ols_fp32_w<N, 4, false, false>(a, sms, max_ctas, st, grid_out);
+    }
+    if constexpr (N == 1024) {
+        // signals in host memory: consecutive blocks of a warp pass their overlap samples in
+        // registers instead of reading them over the host link again
+        if (b && (a.flags & kOlsNoBulk)) {
+            switch (warps) {
+            case 4: return launch_ols_fp32_w<N, 4, true, true, false, true>(a, sms, max_ctas, st, grid_out);
+            case 8: return launch_ols_fp32_w<N, 8, true, true, false, true>(a, sms, max_ctas, st, grid_out);
+            default: return cudaErrorInvalidValue;
+            }
+        }
     }
     switch (warps) {
     case 4: return b ? launch_ols_fp32_w<N, 4, true, true>(a, sms, max_ctas, st, grid_out)
