@@ -189,22 +189,21 @@ __device__ __forceinline__ float4 lds_f4(uint32_t a)
     return v;
 }
 
-// One forward N-point four-step DFT on the register array x (see the top of this file):
-// in:  x[n1] = u(T n1 + t)
-// out: x[n1] = U(T n1 + t)      (with n1 = s + S k', this is X(ka + E k') for ka = s T + t)
-// F1 E-point DFT, F2 twiddle, F3 transpose through buf, F4 S T-point DFTs.
-template <int N>
-__device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2* buf,
-                                              const float4* twrow, int t)
+// F2 and F3 of the four-step DFT below: the twiddle W_N^{t ka} (row t of the table), then the
+// transpose through buf, after which register SS + S k' holds row ka = SS T + t, column n2 = k'.
+// TW0: the table's ka = 0 entries are not 1 (a table that carries an extra per-thread factor), so
+// F2 multiplies them too; otherwise that multiply is skipped.
+template <int N, bool TW0 = false>
+__device__ __forceinline__ void four_step_f2f3(float2 (&x)[OlsGeom<N>::E], float2* buf,
+                                               const float4* twrow, int t)
 {
     using G = OlsGeom<N>;
     constexpr int E = G::E, T = G::T, S = G::S, ROW = G::ROW;
-    fft_reg<E, false>(x);                                                    // F1
     const uint32_t tr = smem_u32(twrow);
     static_for<0, E / 2>([&](auto kh) {                                      // F2
         constexpr int ka = 2 * decltype(kh)::value;
         const float4 w = lds_f4(tr + 16 * decltype(kh)::value);
-        if constexpr (ka != 0) x[ka] = cmul(x[ka], make_float2(w.x, w.y));
+        if constexpr (ka != 0 || TW0) x[ka] = cmul(x[ka], make_float2(w.x, w.y));
         x[ka + 1] = cmul(x[ka + 1], make_float2(w.z, w.w));
     });
     if constexpr (!G::HALF) {
@@ -244,6 +243,20 @@ __device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2
             });
         });
     }
+}
+
+// One forward N-point four-step DFT on the register array x (see the top of this file):
+// in:  x[n1] = u(T n1 + t)
+// out: x[n1] = U(T n1 + t)      (with n1 = s + S k', this is X(ka + E k') for ka = s T + t)
+// F1 E-point DFT, F2 twiddle, F3 transpose through buf, F4 S T-point DFTs.
+template <int N, bool TW0 = false>
+__device__ __forceinline__ void four_step_dft(float2 (&x)[OlsGeom<N>::E], float2* buf,
+                                              const float4* twrow, int t)
+{
+    using G = OlsGeom<N>;
+    constexpr int E = G::E, T = G::T, S = G::S;
+    fft_reg<E, false>(x);                                                    // F1
+    four_step_f2f3<N, TW0>(x, buf, twrow, t);                                // F2, F3
     static_for<0, S>([&](auto s) {
         constexpr int SS = decltype(s)::value;
         float2 c[T];

@@ -30,6 +30,10 @@ size_t ols_warp_bytes(int N);
 cudaError_t launch_ols_tc(int N, int prec, const OlsArgs& a, int sms, cudaStream_t st);
 size_t tc_table_bytes(int N, int prec);
 cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st);
+int split2048_table_entries();
+cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
+cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
+                                 int* grid_out);
 constexpr int kTcTileBlocks = 8;
 }  // namespace vbw
 
@@ -249,6 +253,17 @@ static int ctas_cap_for(int N, int sms)
     return (i >= 0 && g_tune_ctas[i] > 0) ? g_tune_ctas[i] * sms : 0;
 }
 
+// N = 2048 with overlap N/4 runs the split kernel (two 1024-point halves, one parked in tensor
+// memory; ols_split2048.cu) unless VBW_SPLIT2048=0; VBW_SPLIT2048_WARPS picks 8, 12 or 16 warps
+// per CTA (one CTA per SM).
+static bool split2048_enabled() { return env_int("VBW_SPLIT2048", 1) != 0; }
+
+static int split2048_warps()
+{
+    const int w = env_int("VBW_SPLIT2048_WARPS", 0);
+    return (w == 8 || w == 12 || w == 16) ? w : 12;
+}
+
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st, int max_ctas = 0)
 {
     int grid = 0;
@@ -260,7 +275,10 @@ static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st
     case 256: return launch_ols_fp32<256>(a, warps, sms, max_ctas, st, &grid);
     case 512: return launch_ols_fp32<512>(a, warps, sms, max_ctas, st, &grid);
     case 1024: return launch_ols_fp32<1024>(a, warps, sms, max_ctas, st, &grid);
-    case 2048: return launch_ols_fp32<2048>(a, warps, sms, max_ctas, st, &grid);
+    case 2048:
+        if (a.overlap == 512 && !(a.flags & kOlsReal) && split2048_enabled())
+            return launch_ols_split2048(a, split2048_warps(), sms, max_ctas, st, &grid);
+        return launch_ols_fp32<2048>(a, warps, sms, max_ctas, st, &grid);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -294,6 +312,14 @@ int tile_blocks(const vbw_plan_s* p)
 
 // entries of the per-plan twiddle table: T rows of E + 2 (see OlsGeom::TW)
 static int twiddle_entries(int N) { return layout_T(N) * (N / layout_T(N) + 2); }
+
+// Entries of a plan's twiddle array: the four-step rows, the half-sample phases of an odd
+// overlap, and for N = 2048 with overlap N/4 the split kernel's F2 tables.
+static int plan_twiddle_entries(int N, int overlap)
+{
+    return twiddle_entries(N) + ((overlap & 1) ? half_phase_entries(N) : 0) +
+           ((N == 2048 && overlap == N / 4) ? split2048_table_entries() : 0);
+}
 
 // ------------------------------------------------------------------------------------------------
 // plans
@@ -335,7 +361,7 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
             st = fail(VBW_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
             break;
         }
-        const int tw_total = twiddle_entries(N) + ((overlap & 1) ? half_phase_entries(N) : 0);
+        const int tw_total = plan_twiddle_entries(N, overlap);
         if (cudaMalloc(&p->d_tw, sizeof(float2) * tw_total) != cudaSuccess ||
             cudaMalloc(&p->d_V, sizeof(float) * LV) != cudaSuccess ||
             cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
@@ -353,6 +379,10 @@ extern "C" vbw_status vbw_plan(int N, int overlap, const double* V, int LV, int 
                                                                        N / layout_T(N));
         if (overlap & 1)
             vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256>>>(p->d_tw + twiddle_entries(N), N);
+        if (N == 2048 && overlap == N / 4 && (e = build_split2048_table(p->d_tw + twiddle_entries(N), 0)) != cudaSuccess) {
+            st = fail(VBW_ERR_CUDA, "split twiddle kernel failed: %s", cudaGetErrorString(e));
+            break;
+        }
         if (precision != VBW_PREC_FP32) {
             if (cudaMalloc(&p->d_tc, tc_table_bytes(N, precision)) != cudaSuccess) {
                 cudaGetLastError();

@@ -348,3 +348,41 @@ def test_odd_overlap_batch_real_and_no_alloc(cuda, N, overlap):
     assert_parity(yrd.cpu().numpy(), oracle.filter(N, overlap, V, bands, xr.astype(np.complex64)).real,
                   what="real batch")
     assert_parity(ys.cpu().numpy(), oracle.filter(N, overlap, V, 9, x), what="no-alloc")
+
+
+
+_N2048_CASE = {}
+
+
+def _n2048_case():
+    """Input, band schedule and oracle output shared by the N = 2048 kernel-shape tests."""
+    if not _N2048_CASE:
+        N, O, LV = 2048, 512, 12
+        M = N - O
+        V = wl.transition_table(2048 + 77, LV)
+        nblocks = 3000
+        x = wl.complex_gaussian(2048 + 5, 1, nblocks * M + 777)
+        band0 = 300
+        changes = [(150, 37), (2301, wl.max_band(N, LV)), (2950, 5)]
+        ref = oracle.filter(N, O, V, bands_from_changes(nblocks + 1, band0, changes), x)
+        _N2048_CASE.update(V=V, x=x, band0=band0, changes=changes, nblocks=nblocks, ref=ref)
+    return _N2048_CASE
+
+
+@pytest.mark.parametrize("shape", ["split8", "split12", "split16", "four_step"])
+def test_n2048_kernel_shapes(cuda, monkeypatch, shape):
+    """N = 2048, overlap N/4 runs the split kernel: one radix-2 step into two 1024-point halves,
+    the idle half parked in tensor memory, at 8, 12 or 16 warps per CTA; VBW_SPLIT2048=0 selects
+    the 64 x 32 four-step kernel. Each against the oracle: a first call with more blocks than
+    warps (some warps take two tiles), band changes inside the calls, the stream continued in a
+    second call and a ragged end."""
+    torch = cuda
+    if shape == "four_step":
+        monkeypatch.setenv("VBW_SPLIT2048", "0")
+    else:
+        monkeypatch.setenv("VBW_SPLIT2048", "1")
+        monkeypatch.setenv("VBW_SPLIT2048_WARPS", shape[len("split"):])
+    c = _n2048_case()
+    plan = vbw.Plan(2048, 512, c["V"])
+    y = run_stream(torch, plan, c["x"], c["band0"], changes=c["changes"], chunks=[2600, c["nblocks"] - 2600])
+    assert_parity(y, c["ref"], what=f"N=2048 {shape}")
