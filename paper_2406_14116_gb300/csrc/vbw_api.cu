@@ -31,6 +31,7 @@ cudaError_t launch_ols_tc(int N, int prec, const OlsArgs& a, int sms, cudaStream
 size_t tc_table_bytes(int N, int prec);
 cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st);
 int split2048_table_entries();
+int split2048_choice();
 cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
 cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
                                  int* grid_out);
@@ -263,6 +264,10 @@ static int split2048_warps()
     const int w = env_int("VBW_SPLIT2048_WARPS", 0);
     return (w == 8 || w == 12 || w == 16) ? w : 12;
 }
+
+// The same choice for callers outside this file (vbw_filter_static): warps per CTA of the split
+// kernel, or 0 when the 64 x 32 four-step kernel runs.
+int vbw::split2048_choice() { return split2048_enabled() ? split2048_warps() : 0; }
 
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st, int max_ctas = 0)
 {

@@ -8,7 +8,8 @@
 // one fixed array of device memory that is part of the library image. Every GPU that loads the
 // library holds that array until the process exits.
 //
-// The kernel is the same fused FP32 kernel as every other path (ols_fp32_kernel, single-job form).
+// The kernels are those of every other path (ols_fp32_kernel, and for N = 2048 with overlap N/4 the
+// split kernel of ols_split2048.cu), in their single-job form.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,14 +27,19 @@ template <int N>
 cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
                             int* grid_out);
 vbw_status set_error(vbw_status st, const char* msg);   // vbw_last_error() text (vbw_api.cu)
+int split2048_choice();                                  // vbw_api.cu
+int split2048_table_entries();                           // ols_split2048.cu
+cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
+cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
+                                 int* grid_out);
 }  // namespace vbw
 
 namespace {
 
 // Layout of the scratch (bytes). Sized for the largest plan the library accepts (N = 2048,
 // L_V = N/2 - 2), so every valid request fits.
-constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 float2 = 16896 bytes
-constexpr size_t kTwCap = 32768;
+constexpr size_t kTwOff = 0;           // twiddle rows: at most 32 x 66 float2 = 16896 bytes, then
+constexpr size_t kTwCap = 49152;       // for N = 2048, overlap N/4, the split kernel's 26112 bytes
 constexpr size_t kVOff = kTwOff + kTwCap;    // transition table, float32: at most 4088 bytes
 constexpr size_t kVCap = 8192;
 constexpr size_t kScratchBytes = 64 * 1024;      // the whole array: 64 KiB per GPU
@@ -103,7 +109,9 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     if (band < 1 || band > N / 2 - LV - 1) return fail_static(VBW_ERR_BAND_RANGE, "band outside [1, N/2-L_V-1]");
     if (nsamples < 0) return fail_static(VBW_ERR_INVALID_ARG, "nsamples < 0");
     const int T = layout_T_of(N), E = N / T;
-    const size_t tw_bytes = sizeof(float2) * ((size_t)T * (E + 2) + ((overlap & 1) ? half_phase_entries(N) : 0));
+    const bool split = (N == 2048 && overlap == N / 4);   // the split kernel's tables follow the rows
+    const size_t tw_bytes = sizeof(float2) * ((size_t)T * (E + 2) + ((overlap & 1) ? half_phase_entries(N) : 0) +
+                                              (split ? split2048_table_entries() : 0));
     if (tw_bytes > kTwCap || LV > kMaxLV)
         return fail_static(VBW_ERR_INVALID_ARG, "request exceeds the static scratch (64 KiB)");
     if (nsamples == 0) return vbw::set_error(VBW_OK, "");
@@ -140,6 +148,8 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
             vbw_twiddle_kernel<<<(tw_entries + 255) / 256, 256, 0, s>>>(tw, N, T, E);
             if (overlap & 1)
                 vbw_halfphase_kernel<<<(half_phase_entries(N) + 255) / 256, 256, 0, s>>>(tw + tw_entries, N);
+            if (split && build_split2048_table(tw + tw_entries, s) != cudaSuccess)
+                return fail_static(VBW_ERR_CUDA, "table kernels failed");
             static_round_v_kernel<<<(LV + 255) / 256, 256, 0, s>>>(pv, LV, Vf);
             if (cudaGetLastError() != cudaSuccess) return fail_static(VBW_ERR_CUDA, "table kernels failed");
             k.N = N;
@@ -171,7 +181,11 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     case 256: e = launch_ols_fp32<256>(a, warps, sms, 0, s, &grid); break;
     case 512: e = launch_ols_fp32<512>(a, warps, sms, 0, s, &grid); break;
     case 1024: e = launch_ols_fp32<1024>(a, warps, sms, 0, s, &grid); break;
-    default: e = launch_ols_fp32<2048>(a, warps, sms, 0, s, &grid); break;
+    default: {
+        const int sw = split ? split2048_choice() : 0;
+        e = sw ? launch_ols_split2048(a, sw, sms, 0, s, &grid) : launch_ols_fp32<2048>(a, warps, sms, 0, s, &grid);
+        break;
+    }
     }
     if (e != cudaSuccess) return fail_static(VBW_ERR_CUDA, "filter launch failed");
     return vbw::set_error(VBW_OK, "");
