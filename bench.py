@@ -85,6 +85,7 @@ def parse_args():
 
 KERNEL_SOURCES = ("ols_fp32.cuh", "fft_reg.cuh", "vbw_common.cuh")   # the fused FP32 kernel
 TC_SOURCES = ("ols_tc.cuh", "tc_common.cuh") + KERNEL_SOURCES             # the tensor-core kernel
+SPLIT_SOURCES = ("ols_split2048.cu", "tc_common.cuh") + KERNEL_SOURCES   # N = 2048, overlap N/4
 OLA_SOURCES = KERNEL_SOURCES + ("vbw_ola.cu",)                        # the overlap-add kernel
 
 
@@ -571,6 +572,10 @@ def native_run(args):
     if args.workload == "precision" and args.prec == "bf16" and not args.channels and not args.samples:
         traffic = profile_traffic("ols_tc_n256-512_bf16_precision", TC_SOURCES,
                                   key=f"dram_bytes_per_full_launch_n{args.N}")
+    split2048 = (args.workload == "precision" and args.prec == "fp32" and args.N == 2048 and
+                 os.environ.get("VBW_SPLIT2048", "1") != "0")
+    if split2048 and not args.channels and not args.samples:
+        traffic = profile_traffic("ols_split2048_n2048_precision", SPLIT_SOURCES)
 
     e2e = None
     if not args.no_e2e:
@@ -641,6 +646,7 @@ def native_run(args):
                          "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured"
                          else "fallback 6.8 TB/s",
                          "kernel": ("ols_tc_kernel (tcgen05)" if args.prec != "fp32" else
+                                    "ols_split2048_kernel" if split2048 else
                                     "ols_fp32_kernel" if launches_per_step == 1 else "ols_fp32/ols_mixed kernels"),
                          "launch_ms": step_ms / launches_per_step,
                          "step_ms": step_ms,
