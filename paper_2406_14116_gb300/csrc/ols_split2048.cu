@@ -137,6 +137,24 @@ __device__ __forceinline__ void build_split_gains(float* gtab, int t, int k1, in
     for (int j = t; j < 512; j += 32) gtab[Split::GO + j] = hr_gain(2 * j + 1, k1, LV, V) * inv_n;
 }
 
+// Gains of register n1 of thread t in half h, i.e. of bin K = 2 (32 n1 + t) + h: kk = K below
+// N/2 (n1 < 16), else N - K. Shared-memory addresses of row n1 = 0 on each side.
+struct SplitGainRow {
+    uint32_t lo, hi;
+};
+
+__device__ __forceinline__ SplitGainRow split_gain_row(const float* gtab, int h, int t)
+{
+    const uint32_t gb = smem_u32(gtab + h * Split::GO);
+    return SplitGainRow{gb + 4 * t, gb + 4 * ((1024 - h) - t)};
+}
+
+template <int N1>
+__device__ __forceinline__ float split_gain(const SplitGainRow& g)
+{
+    return (N1 < 16) ? lds_f32(g.lo + 4 * 32 * N1) : lds_f32(g.hi - 4 * 32 * N1);
+}
+
 // One block of N = 2048 per warp. LEAN: a register budget of 128 (16 warps per SM), so the merge
 // reads the parked half back 8 rows at a time instead of all at once.
 template <bool LEAN, class Src>
@@ -271,14 +289,9 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
                     });
                 }
             } else {
-                // register n1 holds bin K = 2 (32 n1 + t) + h; kk = K below N/2, else N - K
-                const int h = step >> 2;
-                const uint32_t gb = smem_u32(gtab + h * Split::GO);
-                const uint32_t lo = gb + 4 * t;
-                const uint32_t hi = gb + 4 * ((1024 - h) - t);
+                const SplitGainRow g = split_gain_row(gtab, step >> 2, t);
                 static_for<0, 32>([&](auto n1) {
-                    constexpr int N1 = decltype(n1)::value;
-                    const float gk = (N1 < 16) ? lds_f32(lo + 4 * 32 * N1) : lds_f32(hi - 4 * 32 * N1);
+                    const float gk = split_gain<decltype(n1)::value>(g);
                     x[n1] = make_float2(gk * x[n1].y, gk * x[n1].x);
                 });
             }
@@ -397,6 +410,22 @@ __global__ void split2048_twiddle_kernel(float2* tw)
     tw[idx] = make_float2((float)c, (float)s);
 }
 
+// Writes the H_R(K) that the split kernel applies for band k1 (test hook): its table build and its
+// register-to-bin mapping, one warp; the tables' 1/N is undone exactly.
+__global__ void split2048_export_hr_kernel(const float* V, int LV, int k1, float* out)
+{
+    __shared__ __align__(16) float gtab[Split::GT];
+    const int t = threadIdx.x;
+    build_split_gains(gtab, t, k1, LV, V);
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+        const SplitGainRow g = split_gain_row(gtab, h, t);
+        static_for<0, 32>([&](auto n1) {
+            out[2 * (32 * decltype(n1)::value + t) + h] = split_gain<decltype(n1)::value>(g) * (float)Split::N;
+        });
+    }
+}
+
 template <int WARPS, bool BATCH>
 cudaError_t launch_split_w(const OlsArgs& a, const float2* tws, int sms, int max_ctas, cudaStream_t st,
                            int* grid_out)
@@ -427,6 +456,12 @@ int split2048_table_entries() { return Split::TW_ENTRIES; }
 cudaError_t build_split2048_table(float2* tw, cudaStream_t st)
 {
     split2048_twiddle_kernel<<<(Split::TW_ENTRIES + 255) / 256, 256, 0, st>>>(tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split2048_export_hr(const float* V, int LV, int k1, float* out, cudaStream_t st)
+{
+    split2048_export_hr_kernel<<<1, 32, 0, st>>>(V, LV, k1, out);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ size_t tc_table_bytes(int N, int prec);
 cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st);
 int split2048_table_entries();
 int split2048_choice();
+cudaError_t launch_split2048_export_hr(const float* V, int LV, int k1, float* out, cudaStream_t st);
 cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
 cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
                                  int* grid_out);
@@ -1428,7 +1429,12 @@ extern "C" vbw_status vbw_debug_export_HR(vbw_plan_t p, int band, float* host_ou
     case 256: e = launch_export_hr<256>(p->d_V, p->LV, band, d, 0); break;
     case 512: e = launch_export_hr<512>(p->d_V, p->LV, band, d, 0); break;
     case 1024: e = launch_export_hr<1024>(p->d_V, p->LV, band, d, 0); break;
-    default: e = launch_export_hr<2048>(p->d_V, p->LV, band, d, 0); break;
+    default:
+        // the kernel this plan's filtering runs: the split kernel's tables and bin mapping for
+        // overlap N/4, else the four-step kernel's
+        e = (p->O == p->N / 4 && split2048_choice()) ? launch_split2048_export_hr(p->d_V, p->LV, band, d, 0)
+                                                      : launch_export_hr<2048>(p->d_V, p->LV, band, d, 0);
+        break;
     }
     if (e == cudaSuccess) e = cudaMemcpy(host_out, d, sizeof(float) * p->N, cudaMemcpyDeviceToHost);
     cudaFree(d);

@@ -75,6 +75,24 @@ def test_band_indexing_bit_exact(cuda, N, LV):
         assert e.value.code == 2
 
 
+@pytest.mark.parametrize("LV", [1, 12, "max"])
+def test_band_indexing_bit_exact_four_step_2048(cuda, monkeypatch, LV):
+    """N = 2048 with overlap N/4 exports the split kernel's gain tables and bin mapping (above);
+    with VBW_SPLIT2048=0 it exports the 64 x 32 four-step kernel's, which also serves other
+    overlaps and real signals. Both must equal eq. (FS_Hk_real) bit for bit."""
+    monkeypatch.setenv("VBW_SPLIT2048", "0")
+    N = 2048
+    LV = N // 2 - 2 - 1 if LV == "max" else LV
+    V = wl.transition_table(300 + LV, LV)
+    plan = vbw.Plan(N, N // 4, V)
+    top = wl.max_band(N, LV)
+    cand = [1, 2, 3, top - 1, top] + list(np.random.default_rng(LV).integers(1, top + 1, 60))
+    for k1 in sorted(set(int(k) for k in cand if 1 <= k <= top)):
+        got = vbw.vbw_debug_export_HR(plan.handle, int(k1))
+        want = oracle.HR(N, V, int(k1)).astype(np.float32)
+        np.testing.assert_array_equal(got, want, err_msg=f"four-step N=2048 L_V={LV} k1={k1}")
+
+
 GEOMS = [(128, 32), (128, 2), (128, 126), (256, 64), (256, 100), (512, 128), (512, 384),
          (1024, 256), (1024, 6), (2048, 512), (2048, 30), (2048, 1800)]
 
