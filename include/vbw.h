@@ -219,7 +219,8 @@ vbw_status vbw_debug_tc_gemm(int flags, int K, int NN, const float* A, const flo
 
 /* Test hook: writes the H_R(k) values (k = 0..N-1) that the filtering kernel applies for `band`,
  * produced by the same device code and register layout, to host_out (N floats). For N = 2048 with
- * overlap N/4 that is the split kernel's (two de-interleaved tables, bins 2k and 2k + 1).
+ * overlap N/4 that is the split kernel's (two de-interleaved tables, bins 2k and 2k + 1), which
+ * filters every launch that fills the GPU; shorter launches use the four-step kernel's layout.
  * Synchronous. */
 vbw_status vbw_debug_export_HR(vbw_plan_t plan, int band, float* host_out);
 

@@ -746,10 +746,8 @@ template <class Kern>
 cudaError_t launch_persistent(Kern kern, int warps, size_t smem, int64_t ntiles, int sms, int max_ctas,
                               cudaStream_t st, int* grid_out, const void* arg_ptr)
 {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    cudaError_t e = prepared_occupancy((const void*)kern, warps * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t ctas_needed = (ntiles + warps - 1) / warps;

@@ -432,10 +432,8 @@ cudaError_t launch_split_w(const OlsArgs& a, const float2* tws, int sms, int max
 {
     auto kern = ols_split2048_kernel<WARPS, BATCH>;
     const size_t smem = Split::TW_BYTES + (size_t)WARPS * Split::WARP_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    cudaError_t e = prepared_occupancy((const void*)kern, WARPS * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t ctas_needed = (a.ntiles + WARPS - 1) / WARPS;

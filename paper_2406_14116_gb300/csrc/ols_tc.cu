@@ -1,5 +1,6 @@
 // Tensor-core (tcgen05) OLS kernels for N = 256 and 512 (overlap N/4), their per-plan tables, and
 // a GEMM test hook that checks the UMMA operand layout against a host GEMM.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdlib>
@@ -15,24 +16,31 @@ static cudaError_t launch_tc_w(const OlsArgs& a, int sms, cudaStream_t st)
 {
     using G = TcSmem<N, PREC>;
     auto kern = ols_tc_kernel<N, PREC, BATCH>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES);
+    cudaError_t e = ensure_smem_limit((const void*)kern, G::BYTES);
     if (e != cudaSuccess) return e;
     // Resident CTAs per SM, from the SM's shared memory, registers and threads. (The occupancy
     // calculator reports one CTA per SM for this kernel, while four fit and run concurrently:
     // measured 43 -> 127 Gsamples/s for BF16 x3 at N = 256.) VBW_TC_CTAS (1..8) overrides it. At
-    // most the TMEM columns of one SM allow: every CTA holds kTcTmemCols.
-    int dev = 0, smem_sm = 0, smem_rsv = 0;
-    cudaFuncAttributes fa;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
-        return e;
-    int per_sm = smem_sm / (int)(G::BYTES + smem_rsv);
-    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
-    if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
-    if (2048 / kTcThreads < per_sm) per_sm = 2048 / kTcThreads;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // most the TMEM columns of one SM allow: every CTA holds kTcTmemCols. Worked out once per
+    // device (the runtime queries cost microseconds per launch).
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    static std::atomic<int> fits[64];
+    int per_sm = (dev >= 0 && dev < 64) ? fits[dev].load(std::memory_order_relaxed) : 0;
+    if (per_sm == 0) {
+        int smem_sm = 0, smem_rsv = 0;
+        cudaFuncAttributes fa;
+        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
+            return e;
+        per_sm = smem_sm / (int)(G::BYTES + smem_rsv);
+        const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+        if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
+        if (2048 / kTcThreads < per_sm) per_sm = 2048 / kTcThreads;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (dev >= 0 && dev < 64) fits[dev].store(per_sm, std::memory_order_relaxed);
+    }
     static const int env_ctas = [] {
         const char* v = getenv("VBW_TC_CTAS");
         const int c = v ? atoi(v) : 0;

@@ -31,7 +31,7 @@ cudaError_t launch_ols_tc(int N, int prec, const OlsArgs& a, int sms, cudaStream
 size_t tc_table_bytes(int N, int prec);
 cudaError_t build_tc_table(int N, int prec, unsigned char* out, cudaStream_t st);
 int split2048_table_entries();
-int split2048_choice();
+int split2048_choice(int64_t ntiles, int sms);
 cudaError_t launch_split2048_export_hr(const float* V, int LV, int k1, float* out, cudaStream_t st);
 cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
 cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
@@ -256,9 +256,18 @@ static int ctas_cap_for(int N, int sms)
 }
 
 // N = 2048 with overlap N/4 runs the split kernel (two 1024-point halves, one parked in tensor
-// memory; ols_split2048.cu) unless VBW_SPLIT2048=0; VBW_SPLIT2048_WARPS picks 8, 12 or 16 warps
-// per CTA (one CTA per SM).
+// memory; ols_split2048.cu) when a launch has at least one tile per warp of the GPU at the split
+// kernel's shape. Smaller launches are latency-bound: a warp then works through a single tile, and
+// the split kernel's tile, 12 warps to an SM, takes longer than the four-step kernel's (serving
+// p50 85 -> 96 us with the split kernel on every launch). VBW_SPLIT2048=0 never runs it, =2 runs
+// it for every size; VBW_SPLIT2048_WARPS picks 8, 12 or 16 warps per CTA (one CTA per SM).
 static bool split2048_enabled() { return env_int("VBW_SPLIT2048", 1) != 0; }
+
+static bool split2048_for(int64_t ntiles, int sms, int warps)
+{
+    const int mode = env_int("VBW_SPLIT2048", 1);
+    return mode == 2 || (mode != 0 && ntiles >= (int64_t)sms * warps);
+}
 
 static int split2048_warps()
 {
@@ -267,8 +276,13 @@ static int split2048_warps()
 }
 
 // The same choice for callers outside this file (vbw_filter_static): warps per CTA of the split
-// kernel, or 0 when the 64 x 32 four-step kernel runs.
-int vbw::split2048_choice() { return split2048_enabled() ? split2048_warps() : 0; }
+// kernel, or 0 when the 64 x 32 four-step kernel runs, for a launch of ntiles tiles (ntiles < 0:
+// whether the split kernel runs for some size, which decides the H_R export's layout).
+int vbw::split2048_choice(int64_t ntiles, int sms)
+{
+    if (ntiles < 0) return split2048_enabled() ? split2048_warps() : 0;
+    return split2048_for(ntiles, sms, split2048_warps()) ? split2048_warps() : 0;
+}
 
 static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st, int max_ctas = 0)
 {
@@ -282,7 +296,7 @@ static cudaError_t launch_fp32(int N, const OlsArgs& a, int sms, cudaStream_t st
     case 512: return launch_ols_fp32<512>(a, warps, sms, max_ctas, st, &grid);
     case 1024: return launch_ols_fp32<1024>(a, warps, sms, max_ctas, st, &grid);
     case 2048:
-        if (a.overlap == 512 && !(a.flags & kOlsReal) && split2048_enabled())
+        if (a.overlap == 512 && !(a.flags & kOlsReal) && split2048_for(a.ntiles, sms, split2048_warps()))
             return launch_ols_split2048(a, split2048_warps(), sms, max_ctas, st, &grid);
         return launch_ols_fp32<2048>(a, warps, sms, max_ctas, st, &grid);
     default: return cudaErrorInvalidValue;
@@ -1432,7 +1446,7 @@ extern "C" vbw_status vbw_debug_export_HR(vbw_plan_t p, int band, float* host_ou
     default:
         // the kernel this plan's filtering runs: the split kernel's tables and bin mapping for
         // overlap N/4, else the four-step kernel's
-        e = (p->O == p->N / 4 && split2048_choice()) ? launch_split2048_export_hr(p->d_V, p->LV, band, d, 0)
+        e = (p->O == p->N / 4 && split2048_choice(-1, p->sms)) ? launch_split2048_export_hr(p->d_V, p->LV, band, d, 0)
                                                       : launch_export_hr<2048>(p->d_V, p->LV, band, d, 0);
         break;
     }

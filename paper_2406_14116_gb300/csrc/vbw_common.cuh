@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 namespace vbw {
 
@@ -160,5 +162,75 @@ struct MixedArgs {
     int32_t warp_bytes;   // per-warp region (largest N of the launch)
     int32_t flags;        // as OlsArgs::flags
 };
+
+// ---------------------------------------------------------------------------------------------
+// Launch preparation of the persistent kernels (host). Raising a kernel's dynamic shared-memory
+// limit and asking how many CTAs fit per SM are two runtime calls that cost microseconds, most of
+// a small launch. Both answers are kept per (device, kernel, block size, shared memory). A
+// kernel's limit only ever rises, so a launch prepared earlier with more shared memory stays
+// valid. The state belongs to the devices' current contexts, like the plans: a device reset
+// invalidates both.
+struct LaunchPrep {
+    int dev;
+    const void* kern;
+    int threads;
+    size_t smem;
+    int per_sm;
+};
+
+struct SmemLimit {
+    int dev;
+    const void* kern;
+    size_t smem;
+};
+
+inline std::mutex& launch_prep_mutex()
+{
+    static std::mutex mu;
+    return mu;
+}
+
+// Raises kern's dynamic shared-memory limit on the current device to at least smem.
+inline cudaError_t ensure_smem_limit(const void* kern, size_t smem)
+{
+    static std::vector<SmemLimit> limits;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(launch_prep_mutex());
+    SmemLimit* lim = nullptr;
+    for (SmemLimit& l : limits)
+        if (l.dev == dev && l.kern == kern) lim = &l;
+    if (lim && lim->smem >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (lim) lim->smem = smem;
+    else limits.push_back(SmemLimit{dev, kern, smem});
+    return cudaSuccess;
+}
+
+// CTAs of `threads` threads with `smem` dynamic shared memory that fit per SM, the limit raised.
+inline cudaError_t prepared_occupancy(const void* kern, int threads, size_t smem, int* per_sm)
+{
+    static std::vector<LaunchPrep> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(launch_prep_mutex());
+        for (const LaunchPrep& c : cache)
+            if (c.dev == dev && c.kern == kern && c.threads == threads && c.smem == smem) {
+                *per_sm = c.per_sm;
+                return cudaSuccess;
+            }
+    }
+    if ((e = ensure_smem_limit(kern, smem)) != cudaSuccess) return e;
+    int n = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(launch_prep_mutex());
+    cache.push_back(LaunchPrep{dev, kern, threads, smem, n});
+    *per_sm = n;
+    return cudaSuccess;
+}
 
 }  // namespace vbw

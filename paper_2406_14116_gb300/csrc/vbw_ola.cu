@@ -237,10 +237,8 @@ cudaError_t launch_ola(const OlaArgs& a, int sms, cudaStream_t st)
     const size_t smem = sizeof(float2) * G::TW + (size_t)WARPS * (G::WARP_BYTES +
                         (size_t)OlaGeom<N>::SLOTS * a.slot_bytes);
     auto kern = (a.O == N / 4) ? ola_fp32_kernel<N, WARPS, true> : ola_fp32_kernel<N, WARPS, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    cudaError_t e = prepared_occupancy((const void*)kern, WARPS * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t need = (a.ntiles + WARPS - 1) / WARPS;

@@ -27,7 +27,7 @@ template <int N>
 cudaError_t launch_ols_fp32(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
                             int* grid_out);
 vbw_status set_error(vbw_status st, const char* msg);   // vbw_last_error() text (vbw_api.cu)
-int split2048_choice();                                  // vbw_api.cu
+int split2048_choice(int64_t ntiles, int sms);           // vbw_api.cu
 int split2048_table_entries();                           // ols_split2048.cu
 cudaError_t build_split2048_table(float2* tw, cudaStream_t st);
 cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_ctas, cudaStream_t st,
@@ -182,7 +182,7 @@ extern "C" vbw_status vbw_filter_static(int N, int overlap, const double* V, int
     case 512: e = launch_ols_fp32<512>(a, warps, sms, 0, s, &grid); break;
     case 1024: e = launch_ols_fp32<1024>(a, warps, sms, 0, s, &grid); break;
     default: {
-        const int sw = split ? split2048_choice() : 0;
+        const int sw = split ? split2048_choice(a.ntiles, sms) : 0;
         e = sw ? launch_ols_split2048(a, sw, sms, 0, s, &grid) : launch_ols_fp32<2048>(a, warps, sms, 0, s, &grid);
         break;
     }

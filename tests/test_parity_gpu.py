@@ -389,16 +389,17 @@ def _n2048_case():
 
 @pytest.mark.parametrize("shape", ["split8", "split12", "split16", "four_step"])
 def test_n2048_kernel_shapes(cuda, monkeypatch, shape):
-    """N = 2048, overlap N/4 runs the split kernel: one radix-2 step into two 1024-point halves,
-    the idle half parked in tensor memory, at 8, 12 or 16 warps per CTA; VBW_SPLIT2048=0 selects
-    the 64 x 32 four-step kernel. Each against the oracle: a first call with more blocks than
-    warps (some warps take two tiles), band changes inside the calls, the stream continued in a
-    second call and a ragged end."""
+    """N = 2048, overlap N/4: the split kernel (one radix-2 step into two 1024-point halves, the
+    idle half parked in tensor memory) at 8, 12 or 16 warps per CTA, forced for every launch size
+    (VBW_SPLIT2048=2; by default only launches that fill the GPU take it), and the 64 x 32
+    four-step kernel (VBW_SPLIT2048=0). Each against the oracle: a first call with more blocks
+    than warps (some warps take two tiles), band changes inside the calls, the stream continued
+    in a second call and a ragged end."""
     torch = cuda
     if shape == "four_step":
         monkeypatch.setenv("VBW_SPLIT2048", "0")
     else:
-        monkeypatch.setenv("VBW_SPLIT2048", "1")
+        monkeypatch.setenv("VBW_SPLIT2048", "2")
         monkeypatch.setenv("VBW_SPLIT2048_WARPS", shape[len("split"):])
     c = _n2048_case()
     plan = vbw.Plan(2048, 512, c["V"])
