@@ -22,8 +22,8 @@
 //
 // Tensor memory: b waits there while the even half runs, then the even half's output waits there
 // while the odd half runs. Each warp owns 2 x 64 columns of its 32 lanes (lanes 32 (w mod 4) ..,
-// columns 128 (w div 4) ..), so a 16-warp CTA takes all 512 columns of its SM. The register
-// budget per thread then holds 32 complex values instead of 64.
+// columns 128 (w div 4) ..): the default 12-warp CTA holds 384 of the SM's 512 columns, a 16-warp
+// CTA all of them. The register budget per thread then holds 32 complex values instead of 64.
 #include "ols_fp32.cuh"
 #include "tc_common.cuh"
 
@@ -298,8 +298,8 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
         }
     }
 
-    // ---- merge, discard and store (steps 4-5): x holds W_2048^{t} swap(o) per register, the
-    //      even half's swap(e) is in tensor memory
+    // ---- merge, discard and store (Sec. II steps 4-5): x holds W_2048^{t} swap(o) per register,
+    //      the even half's swap(e) is in tensor memory
     const int64_t blk = kblk;
     const int64_t nsamp = knsamp;
     const bool act = blk * M < nsamp;
