@@ -53,7 +53,7 @@ typedef enum {
     VBW_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                          */
     VBW_ERR_BUSY = 6,        /* no free slot or memory for the request right now            */
     VBW_ERR_STATE = 7,       /* call not allowed in the object's current state              */
-    VBW_ERR_UNSUPPORTED = 8  /* valid request that this build does not provide              */
+    VBW_ERR_UNSUPPORTED = 8  /* valid request that the library does not provide             */
 } vbw_status;
 
 /* Arithmetic of a plan's DFT stages:
