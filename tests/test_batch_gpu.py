@@ -237,6 +237,30 @@ def test_misaligned_pointer_is_rejected(cuda):
     assert e.value.code == 1
 
 
+def test_run_host_zero_copy_split_kernel(cuda, monkeypatch):
+    """N = 2048 batches through the split kernel (forced for this size) with pinned host buffers:
+    the kernel reads and writes host memory directly (no L2 prefetch), and the output equals the
+    device path's bit for bit and the oracle within the FP32 gate."""
+    monkeypatch.setenv("VBW_SPLIT2048", "2")
+    torch = cuda
+    V = wl.transition_table(58, 12)
+    plan = vbw.Plan(2048, 512, V)
+    rng = np.random.default_rng(58)
+    xs = [wl.complex_gaussian(58, i, int(n)) for i, n in enumerate(rng.integers(1000, 60000, 5))]
+    bands = [int(b) for b in rng.integers(1, wl.max_band(2048, 12) + 1, 5)]
+    dx = [torch.from_numpy(x).cuda() for x in xs]
+    dy = [torch.full_like(x, float("nan")) for x in dx]
+    b = vbw.Batch([(plan, x, y, k) for x, y, k in zip(dx, dy, bands)])
+    b.run()
+    torch.cuda.synchronize()
+    hin = [torch.from_numpy(x).pin_memory() for x in xs]
+    hout = [torch.zeros_like(h).pin_memory() for h in hin]
+    b.run_host([h.numpy() for h in hin], [h.numpy() for h in hout])
+    for x, y, h, k in zip(xs, dy, hout, bands):
+        np.testing.assert_array_equal(y.cpu().numpy(), h.numpy())
+        assert_parity(h.numpy(), oracle.filter(2048, 512, V, k, x), what="split zero copy")
+
+
 def test_run_host_zero_copy_matches_device_path(cuda):
     """Pinned host buffers: the kernels work on host memory directly (zero copy); pageable
     buffers: staged copies. Both give the device path's output bit for bit."""

@@ -153,6 +153,22 @@ def test_serving_matches_oracle_per_stream(cuda, plans):
         assert_parity(s["y"], ref, what=f"stream {i} (N={s['N']}, O={s['O']})")
 
 
+def test_serving_split_kernel_for_n2048(cuda, plans, monkeypatch):
+    """The serving engine's N = 2048 launches through the split kernel (forced for these small
+    batches; by default only launches that fill the GPU take it): per-stream oracle parity."""
+    monkeypatch.setenv("VBW_SPLIT2048", "2")
+    vbw, V, geo, ps = plans
+    rng = np.random.default_rng(57)
+    specs = [s for s in _specs(rng, geo, 16) if s[1] == 2048][:4]
+    assert specs, "the seed must draw N = 2048 streams"
+    streams = _make_streams(57, specs, cuda)
+    _serve(vbw, ps, streams, pool_bytes=64 << 20, slots=2, order=_order(streams, rng))
+    for i, s in enumerate(streams):
+        M = s["N"] - s["O"]
+        bands, _ = _expected_bands(M, s["band0"], s["chunks"])
+        assert_parity(s["y"], oracle.filter(s["N"], s["O"], V, bands, s["x"]), what=f"split stream {i}")
+
+
 def test_alone_vs_mix_bitwise(cuda, plans):
     vbw, V, geo, ps = plans
     rng = np.random.default_rng(52)

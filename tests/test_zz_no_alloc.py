@@ -56,6 +56,26 @@ def test_no_alloc_matches_existing_entry_point_on_two_calls(cuda):
 
 
 @pytest.mark.gpu
+def test_no_alloc_split_kernel_equals_batch_path(cuda, monkeypatch):
+    """N = 2048 with overlap N/4 through the split kernel (forced for this size): the no-alloc call
+    and a one-signal batch run the same kernel on the same data, so their outputs are identical."""
+    monkeypatch.setenv("VBW_SPLIT2048", "2")
+    torch = cuda
+    L = vbw.lib()
+    stream = torch.cuda.current_stream()
+    N, O, band, n = 2048, 512, 700, 400_000 + 123
+    V = wl.transition_table(46, 12)
+    x = torch.from_numpy(wl.complex_gaussian(46, 0, n)).cuda()
+    y_static = torch.full_like(x, float("nan"))
+    assert _call(L, N, O, V, band, x.data_ptr(), y_static.data_ptr(), n, stream.cuda_stream) == 0
+    plan = vbw.Plan(N, O, V)
+    y_ref = torch.full_like(x, float("nan"))
+    vbw.Batch([(plan, x, y_ref, band)]).run(stream)
+    torch.cuda.synchronize()
+    assert torch.equal(y_static.view(torch.float32), y_ref.view(torch.float32))
+
+
+@pytest.mark.gpu
 def test_no_alloc_call_leaves_device_memory_unchanged(cuda):
     """After a warm-up call, a call with another geometry (so its tables are rebuilt) and a call
     that repeats it (tables reused) leave the device's free memory exactly where it was."""
