@@ -60,28 +60,42 @@ def _channel_batch(torch, N: int, nch: int, nsamples: int):
     return plan, x, y, vbw.Batch(rows)
 
 
+def _probe_shapes(torch, N: int, nch: int, nsamples: int, reps: int, stream) -> dict:
+    plan, x, y, batch = _channel_batch(torch, N, nch, nsamples)
+    table = []
+    best = None
+    for w in WARPS:
+        for c in CTAS:
+            vbw.vbw_tune_set(N, w, c)
+            ms = _time_ms(torch, lambda: batch.run(stream), reps, stream)
+            gsps = nch * nsamples / (ms * 1e-3) / 1e9
+            table.append({"warps": w, "ctas_per_sm": c, "ms": ms, "gsps": gsps})
+            if best is None or ms < best["ms"]:
+                best = table[-1]
+    vbw.vbw_tune_set(N, 0, 0)
+    batch.close()
+    plan.close()
+    return {"warps": best["warps"], "ctas_per_sm": best["ctas_per_sm"], "gsps": best["gsps"], "table": table}
+
+
 def tune_shapes(torch, Ns=ALL_N, nch: int = 16, nsamples: int = 1 << 21, reps: int = 15) -> dict:
-    """{N: {"warps", "ctas_per_sm", "gsps", "table"}} for the single-plan kernel."""
+    """{N: {"warps", "ctas_per_sm", "gsps", "table"}} for the single-plan kernel. For N = 2048 that
+    is the 64 x 32 four-step kernel (launches that take the split kernel use its own 12-warp
+    shape), so its probe runs with the split kernel switched off."""
     stream = torch.cuda.current_stream()
     out = {}
     for N in Ns:
-        plan, x, y, batch = _channel_batch(torch, N, nch, nsamples)
-        table = []
-        best = None
-        for w in WARPS:
-            for c in CTAS:
-                vbw.vbw_tune_set(N, w, c)
-                ms = _time_ms(torch, lambda: batch.run(stream), reps, stream)
-                gsps = nch * nsamples / (ms * 1e-3) / 1e9
-                table.append({"warps": w, "ctas_per_sm": c, "ms": ms, "gsps": gsps})
-                if best is None or ms < best["ms"]:
-                    best = table[-1]
-        vbw.vbw_tune_set(N, 0, 0)
-        out[str(N)] = {"warps": best["warps"], "ctas_per_sm": best["ctas_per_sm"],
-                       "gsps": best["gsps"], "table": table}
-        batch.close()
-        plan.close()
-        del x, y
+        prev = os.environ.get("VBW_SPLIT2048")
+        if N == 2048:
+            os.environ["VBW_SPLIT2048"] = "0"
+        try:
+            out[str(N)] = _probe_shapes(torch, N, nch, nsamples, reps, stream)
+        finally:
+            if N == 2048:
+                if prev is None:
+                    os.environ.pop("VBW_SPLIT2048", None)
+                else:
+                    os.environ["VBW_SPLIT2048"] = prev
     return out
 
 

@@ -1,6 +1,8 @@
 """Batched filtering of many streams with mixed lengths, transform sizes and bands (one prepared
 batch, single-plan or mixed-plan persistent launches, CUDA-graph replay), the bounded-wait failure
 path, all through the C ABI and checked against the FP64 oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -281,3 +283,19 @@ def test_run_host_zero_copy_matches_device_path(cuda):
         b.run_host(pin, pout)
         for a, h in zip(dev, pout):
             np.testing.assert_array_equal(a, h)
+
+
+def test_tune_shapes_n2048_probes_four_step_and_restores_switch(cuda, monkeypatch):
+    """The autotuner's N = 2048 probe runs the 64 x 32 four-step kernel (the shape it sets is that
+    kernel's; the split kernel has its own) and leaves the VBW_SPLIT2048 setting as it found it."""
+    from paper_2406_14116_gb300 import tune
+    torch = cuda
+    monkeypatch.setenv("VBW_SPLIT2048", "2")
+    out = tune.tune_shapes(torch, Ns=(2048,), nch=2, nsamples=1 << 16, reps=2)
+    assert os.environ["VBW_SPLIT2048"] == "2"
+    d = out["2048"]
+    assert d["warps"] in tune.WARPS and d["ctas_per_sm"] in tune.CTAS
+    assert len(d["table"]) == len(tune.WARPS) * len(tune.CTAS) and all(r["ms"] > 0 for r in d["table"])
+    monkeypatch.delenv("VBW_SPLIT2048")
+    tune.tune_shapes(torch, Ns=(2048,), nch=2, nsamples=1 << 16, reps=2)
+    assert "VBW_SPLIT2048" not in os.environ
