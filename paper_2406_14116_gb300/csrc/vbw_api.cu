@@ -256,17 +256,27 @@ static int ctas_cap_for(int N, int sms)
 }
 
 // N = 2048 with overlap N/4 runs the split kernel (two 1024-point halves, one parked in tensor
-// memory; ols_split2048.cu) when a launch has at least one tile per warp of the GPU at the split
-// kernel's shape. Smaller launches are latency-bound: a warp then works through a single tile, and
-// the split kernel's tile, 12 warps to an SM, takes longer than the four-step kernel's (serving
-// p50 85 -> 96 us with the split kernel on every launch). VBW_SPLIT2048=0 never runs it, =2 runs
-// it for every size; VBW_SPLIT2048_WARPS picks 8, 12 or 16 warps per CTA (one CTA per SM).
+// memory; ols_split2048.cu) when it is expected to finish first. A persistent launch lasts about as
+// long as its busiest warp: ceil(tiles / warp slots) tiles. The four-step kernel has 8 warps per SM,
+// the split kernel 12, and a split-kernel tile takes about 1.35 four-step tile times (its warps
+// share an SM twelve ways; the ratio of the two kernels' large-launch throughputs, 195 / 176
+// Gsamples/s, gives it). In a sweep of launch sizes (8, 16, 32, 48, 64, 128 and 512 channels of
+// 2^16 samples) this estimate picked the faster kernel every time: the four-step kernel below one
+// split wave (serving's batches) and just past a wave boundary, the split kernel otherwise and
+// for large launches (10% faster at 512 channels).
+// VBW_SPLIT2048=0 never runs it, =2 runs it for every size; VBW_SPLIT2048_WARPS picks 8, 12 or 16
+// warps per CTA (one CTA per SM).
 static bool split2048_enabled() { return env_int("VBW_SPLIT2048", 1) != 0; }
 
 static bool split2048_for(int64_t ntiles, int sms, int warps)
 {
     const int mode = env_int("VBW_SPLIT2048", 1);
-    return mode == 2 || (mode != 0 && ntiles >= (int64_t)sms * warps);
+    if (mode == 2) return true;
+    if (mode == 0 || ntiles <= 0 || sms <= 0) return false;
+    const int64_t slots4 = (int64_t)sms * 8, slots_s = (int64_t)sms * warps;
+    const double t4 = (double)((ntiles + slots4 - 1) / slots4);
+    const double ts = 1.35 * (warps / 12.0) * (double)((ntiles + slots_s - 1) / slots_s);
+    return ts < t4;
 }
 
 static int split2048_warps()
