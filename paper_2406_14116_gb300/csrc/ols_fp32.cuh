@@ -642,17 +642,25 @@ __device__ __forceinline__ void ols_fp32_body(const OlsArgs& a)
     const int ph_len = (!QOVL && (a.overlap & 1)) ? half_phase_entries(N) : 0;
     unsigned char* wbase = smem_raw + sizeof(float2) * (G::TW + ph_len) + (size_t)warp * G::WARP_BYTES;
 
+    // job lists: the warp's first tile-list entry is read before the twiddle rows are copied, so
+    // the two reads overlap (the tile loop takes it as its one-tile-ahead entry)
+    int64_t tb, te;
+    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
+    WarpState ws{-1, make_int2(0, 0), false};
+    if constexpr (BATCH) {
+        if (tb < te) {
+            ws.ntd = opaque(a.tiles)[tb];
+            ws.ntd_ok = true;
+        }
+    }
     for (int i = threadIdx.x; i < (G::TW + ph_len) / 2; i += blockDim.x)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(a.tw)[i];
     __syncthreads();
 
-    WarpState ws{-1, make_int2(0, 0), false};
     const TileCtl ctl{(a.flags & kOlsNoBulk) == 0, ph_len ? tw_s + G::TW : nullptr};
     CarryState<CARRY ? G::E / 4 : 0> cs;
     cs.in = nullptr;
     cs.blk = -1;
-    int64_t tb, te;
-    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
         if constexpr (BATCH)
             ols_tile<N, QOVL, JobListSource, REAL, CARRY>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, 0,

@@ -360,6 +360,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1) ols_split2048_kernel(const OlsA
     float2* tw_s = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wbase = smem_raw + Split::TW_BYTES + (size_t)warp * Split::WARP_BYTES;
+    // job lists: the warp's first tile-list entry is read before the tables are copied (the tile
+    // loop takes it as its one-tile-ahead entry)
+    int64_t tb, te;
+    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
+    WarpState ws{-1, make_int2(0, 0), false};
+    if constexpr (BATCH) {
+        if (tb < te) {
+            ws.ntd = opaque(a.tiles)[tb];
+            ws.ntd_ok = true;
+        }
+    }
     for (int i = threadIdx.x; i < Split::TW_ENTRIES / 2; i += blockDim.x)
         reinterpret_cast<float4*>(tw_s)[i] = reinterpret_cast<const float4*>(tws)[i];
     if (warp == 0) {
@@ -372,10 +383,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) ols_split2048_kernel(const OlsA
     const uint32_t tP = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
     const uint32_t tQ = tP + 64;
 
-    WarpState ws{-1, make_int2(0, 0), false};
     const bool bulk = (a.flags & kOlsNoBulk) == 0;
-    int64_t tb, te;
-    warp_range(a.ntiles, (int64_t)gridDim.x * WARPS, (int64_t)blockIdx.x * WARPS + warp, tb, te);
     for (int64_t tile = tb; tile < te; ++tile) {
         if constexpr (BATCH)
             split_tile<(WARPS > 12)>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, tw_s, a.V, a.LV, wbase,
