@@ -271,12 +271,28 @@ def vbw_batch_run(b: int, cuda_stream=None):
     _check(lib().vbw_batch_run(b, _stream_handle(cuda_stream)))
 
 
+def host_pointers(arrays) -> np.ndarray:
+    """The addresses of C-contiguous numpy arrays, as the pointer array vbw_batch_run_host takes.
+    Building it costs about 1 us per array, so callers that run the same buffers repeatedly
+    make it once and pass it instead of the arrays."""
+    for a in arrays:
+        if not a.flags.c_contiguous:
+            raise ValueError("expected C-contiguous host arrays")
+    return np.array([a.__array_interface__["data"][0] for a in arrays], dtype=np.uintp)
+
+
+def _pointer_array(bufs):
+    if isinstance(bufs, np.ndarray) and bufs.dtype == np.uintp and bufs.ndim == 1:
+        return np.ascontiguousarray(bufs)
+    return host_pointers(bufs)
+
+
 def vbw_batch_run_host(b: int, host_in, host_out, cuda_stream=None):
-    """host_in / host_out: sequences of C-contiguous numpy arrays (one per signal)."""
-    n = len(host_in)
-    ins = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in host_in])
-    outs = (ctypes.c_void_p * max(1, n))(*[a.ctypes.data for a in host_out])
-    _check(lib().vbw_batch_run_host(b, ins, outs, _stream_handle(cuda_stream)))
+    """host_in / host_out: sequences of C-contiguous numpy arrays (one per signal), or their
+    address arrays from host_pointers()."""
+    ins, outs = _pointer_array(host_in), _pointer_array(host_out)
+    _check(lib().vbw_batch_run_host(b, ins.ctypes.data_as(ctypes.c_void_p),
+                                    outs.ctypes.data_as(ctypes.c_void_p), _stream_handle(cuda_stream)))
 
 
 def vbw_batch_destroy(b: int):

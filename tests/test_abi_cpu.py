@@ -74,3 +74,18 @@ def test_valid_plan_without_gpu_reports_cuda_error(L):
     V = np.linspace(0.9, 0.1, 6)
     rc = L.vbw_plan(256, 64, V.ctypes.data_as(ctypes.c_void_p), 6, 0, ctypes.byref(h))
     assert rc == 4 and h.value is None
+
+
+def test_host_pointer_arrays_for_run_host():
+    """vbw_batch_run_host takes the signals' host arrays or, for repeated runs, their address
+    array from host_pointers(): the addresses, in order; non-contiguous arrays are refused."""
+    import numpy as np
+    from paper_2406_14116_gb300 import vbw as V
+    buf = np.zeros(1000, np.complex64)
+    views = [buf[0:10], buf[10:250], buf[250:1000]]
+    p = V.host_pointers(views)
+    assert p.dtype == np.uintp and list(p) == [v.ctypes.data for v in views]
+    assert V._pointer_array(p) is p or np.array_equal(V._pointer_array(p), p)
+    assert np.array_equal(V._pointer_array(views), p)
+    with pytest.raises(ValueError):
+        V.host_pointers([buf[::2]])
