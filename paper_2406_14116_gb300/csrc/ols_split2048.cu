@@ -38,15 +38,29 @@ struct Split {
     static constexpr int GO = 516;                                // odd-bin gains start (floats)
     static constexpr int GT = GO + 512;                           // gains per warp (floats)
     static constexpr size_t BUF_BYTES = sizeof(float2) * OlsGeom<1024>::BLK;
-    static constexpr size_t WARP_BYTES = BUF_BYTES + sizeof(float) * GT;
+    static constexpr size_t CARRY_OFF = BUF_BYTES + sizeof(float) * GT;   // per-warp SplitCarry
+    static constexpr size_t WARP_BYTES = CARRY_OFF + 16;
     static constexpr size_t TW_BYTES = sizeof(float2) * TW_ENTRIES;
     static_assert(GO >= 513 && GO % 4 == 0 && WARP_BYTES % 16 == 0, "gain tables must stay 16-byte aligned");
 };
 
-// Tensor-memory columns of one CTA: 128 per warp of each lane quarter, as a power of two.
-constexpr uint32_t split_cols(int warps)
+// Signals in host memory (CARRY): the last O = 512 samples of a block's span, rows 16..31 of its
+// second half, are the first 512 of the next block's span, rows 0..15 of its first half, in the
+// same lanes. They wait in 32 more tensor-memory columns per warp, so consecutive blocks of a warp
+// read each input sample from the host link once. The block they open, in shared memory per warp:
+struct SplitCarry {
+    const float2* in;     // the signal they belong to; nullptr = none
+    int64_t blk;          // the block whose span starts with them
+};
+
+// Tensor-memory columns per warp: b and the parked even half (2 x 64), plus the carry.
+constexpr int split_warp_cols(bool carry) { return carry ? 160 : 128; }
+
+// Tensor-memory columns of one CTA: the per-warp columns times the warps of each lane quarter, as
+// a power of two.
+constexpr uint32_t split_cols(int warps, bool carry = false)
 {
-    const int need = 128 * ((warps + 3) / 4);
+    const int need = split_warp_cols(carry) * ((warps + 3) / 4);
     uint32_t c = 32;
     while ((int)c < need) c <<= 1;
     return c;
@@ -157,10 +171,10 @@ __device__ __forceinline__ float split_gain(const SplitGainRow& g)
 
 // One block of N = 2048 per warp. LEAN: a register budget of 128 (16 warps per SM), so the merge
 // reads the parked half back 8 rows at a time instead of all at once.
-template <bool LEAN, class Src>
+template <bool LEAN, bool CARRY, class Src>
 __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool has_next, const float2* tw_s,
                                            const float* V, int LV, unsigned char* wbase, int t,
-                                           WarpState& ws, bool bulk, uint32_t tP, uint32_t tQ)
+                                           WarpState& ws, bool bulk, uint32_t tP, uint32_t tQ, uint32_t tC)
 {
     constexpr int N = Split::N, O = Split::O, M = Split::M, D = Split::D;
     float2* buf = reinterpret_cast<float2*>(wbase);
@@ -204,7 +218,23 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
             }
             return v;
         };
-        if (fast) {
+        SplitCarry* cm = reinterpret_cast<SplitCarry*>(wbase + Split::CARRY_OFF);
+        bool carried = false;
+        if constexpr (CARRY) carried = fast && cm->in == job.in && cm->blk == blk;   // same for all lanes
+        if (carried) {
+            // rows 0..15: the previous block's rows 16..31 of its second half, from tensor memory
+            uint32_t r[2][16];
+            tm_ld16(tC, r[0]);
+            tm_ld16(tC + 16, r[1]);
+            tm_wait16(r[0]);
+            tm_wait16(r[1]);
+            static_for<0, 16>([&](auto i) {
+                constexpr int I = decltype(i)::value;
+                x[I] = make_float2(__uint_as_float(r[I / 8][2 * (I % 8)]), __uint_as_float(r[I / 8][2 * (I % 8) + 1]));
+            });
+            const float2* sp = job.in + s0 + t;
+            static_for<16, 32>([&](auto n1) { x[n1] = ld_stream(sp + 32 * decltype(n1)::value); });
+        } else if (fast) {
             const float2* sp = job.in + s0 + t;
             static_for<0, 32>([&](auto n1) { x[n1] = ld_stream(sp + 32 * decltype(n1)::value); });
         } else {
@@ -219,6 +249,15 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
             } else {
                 static_for<0, 8>([&](auto i) { h[i] = fetch(s0 + 1024 + 32 * (8 * C + decltype(i)::value) + t); });
             }
+            if constexpr (CARRY && C >= 2) {
+                // rows 16..31 of the second half open the next block's span
+                uint32_t q[16];
+                static_for<0, 8>([&](auto i) {
+                    q[2 * i] = __float_as_uint(h[i].x);
+                    q[2 * i + 1] = __float_as_uint(h[i].y);
+                });
+                tm_st16(tC + 16 * (C - 2), q);
+            }
             uint32_t r[16];
             static_for<0, 8>([&](auto i) {
                 constexpr int n1 = 8 * C + decltype(i)::value;
@@ -230,6 +269,15 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
             });
             tm_st16(tP + 16 * C, r);
         });
+
+        if constexpr (CARRY) {
+            __syncwarp();
+            if (t == 0) {
+                cm->in = active ? job.in : nullptr;
+                cm->blk = blk + 1;
+            }
+            __syncwarp();
+        }
 
         // ---- L2 prefetch of the samples the warp's next tile adds (16-byte aligned bulk copy)
         if (t == 0 && has_next && bulk) {
@@ -351,12 +399,13 @@ __device__ __forceinline__ void split_tile(const Src& src, int64_t tile, bool ha
 
 // One CTA per SM (its shared memory and tensor memory take the SM); warps walk contiguous tile
 // ranges as in the other fused kernels.
-template <int WARPS, bool BATCH>
+template <int WARPS, bool BATCH, bool CARRY = false>
 __global__ void __launch_bounds__(WARPS * 32, 1) ols_split2048_kernel(const OlsArgs a, const float2* tws)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t tmem_slot;
-    constexpr uint32_t kCols = split_cols(WARPS);
+    constexpr uint32_t kCols = split_cols(WARPS, CARRY);
+    static_assert(split_warp_cols(CARRY) * ((WARPS + 3) / 4) <= 512, "the warps' columns exceed the SM's tensor memory");
     float2* tw_s = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wbase = smem_raw + Split::TW_BYTES + (size_t)warp * Split::WARP_BYTES;
@@ -380,17 +429,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) ols_split2048_kernel(const OlsA
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    const uint32_t tP = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
-    const uint32_t tQ = tP + 64;
+    const uint32_t tP = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) +
+                        (uint32_t)(split_warp_cols(CARRY) * (warp >> 2));
+    const uint32_t tQ = tP + 64, tC = tP + 128;
+    if constexpr (CARRY) {
+        if (lane == 0) reinterpret_cast<SplitCarry*>(wbase + Split::CARRY_OFF)->in = nullptr;
+        __syncwarp();
+    }
 
     const bool bulk = (a.flags & kOlsNoBulk) == 0;
     for (int64_t tile = tb; tile < te; ++tile) {
         if constexpr (BATCH)
-            split_tile<(WARPS > 12)>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, tw_s, a.V, a.LV, wbase,
-                                     lane, ws, bulk, tP, tQ);
+            split_tile<(WARPS > 12), CARRY>(JobListSource{a.jobs, a.tiles}, tile, tile + 1 < te, tw_s, a.V, a.LV,
+                                            wbase, lane, ws, bulk, tP, tQ, tC);
         else
-            split_tile<(WARPS > 12)>(SingleJobSource{a}, tile, tile + 1 < te, tw_s, a.V, a.LV, wbase, lane, ws,
-                                     bulk, tP, tQ);
+            split_tile<(WARPS > 12), false>(SingleJobSource{a}, tile, tile + 1 < te, tw_s, a.V, a.LV, wbase, lane,
+                                            ws, bulk, tP, tQ, tC);
     }
     tc_fence_before_sync();
     __syncthreads();
@@ -434,11 +488,11 @@ __global__ void split2048_export_hr_kernel(const float* V, int LV, int k1, float
     }
 }
 
-template <int WARPS, bool BATCH>
+template <int WARPS, bool BATCH, bool CARRY = false>
 cudaError_t launch_split_w(const OlsArgs& a, const float2* tws, int sms, int max_ctas, cudaStream_t st,
                            int* grid_out)
 {
-    auto kern = ols_split2048_kernel<WARPS, BATCH>;
+    auto kern = ols_split2048_kernel<WARPS, BATCH, CARRY>;
     const size_t smem = Split::TW_BYTES + (size_t)WARPS * Split::WARP_BYTES;
     int per_sm = 0;
     cudaError_t e = prepared_occupancy((const void*)kern, WARPS * 32, smem, &per_sm);
@@ -479,6 +533,10 @@ cudaError_t launch_ols_split2048(const OlsArgs& a, int warps, int sms, int max_c
     if (a.overlap != Split::O || (a.flags & kOlsReal)) return cudaErrorInvalidValue;
     const float2* tws = a.tw + OlsGeom<2048>::TW;
     const bool b = a.jobs != nullptr;
+    // batches in host memory: the overlap samples are carried in tensor memory (8 or 12 warps)
+    if (b && (a.flags & kOlsNoBulk) && warps <= 12)
+        return warps == 8 ? launch_split_w<8, true, true>(a, tws, sms, max_ctas, st, grid_out)
+                          : launch_split_w<12, true, true>(a, tws, sms, max_ctas, st, grid_out);
     switch (warps) {
     case 8: return b ? launch_split_w<8, true>(a, tws, sms, max_ctas, st, grid_out)
                      : launch_split_w<8, false>(a, tws, sms, max_ctas, st, grid_out);
